@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark of the SNAP alignment hot path on GB300.
+
+One step = one alignment batch of the workload's reads (1M x 100 bp for the default
+repeat-rich 100 Mbp workload) through the whole path: batch statistics, read
+packing, seed probes, voting, bounded edit distances, hit selection.  The index is
+built once before timing (its build time is reported separately, as the paper
+times alignment separately from index construction).
+
+value: reads/s with the reads already resident in HBM (CUDA events on the launch
+stream, L2 flushed between steps).  e2e: the same metric through snap_align with
+pinned host buffers (host-to-device copy of the reads and device-to-host copy of
+the results inside the timed region).  roofline: the main align kernel's
+algorithmic bytes (from the kernel's own counters) over its event-timed duration,
+against the measured HBM copy bandwidth.  cpu_baseline: the CPU oracle on a bounded
+sample of the same reads, all host cores, whose results are also compared with the
+GPU's (parity_sample).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (replicas; each rank aligns its own reads against its own copy of the
+index, no collective on the data path) runs under torch.distributed.run.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "reads/s aligned on 1 GB300 (bit-exact vs oracle) vs plain form; p50/p99 latency"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="C2")
+    ap.add_argument("--form", choices=["batched", "plain"], default="batched")
+    ap.add_argument("--reads", type=int, default=0, help="override reads per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    return args
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_1111_5572_gb300", "csrc")
+    for fn in sorted(os.listdir(cs)):
+        with open(os.path.join(cs, fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if taken on these sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d.get(kernel)
+        if ent and ent.get("source_hash") == _kernel_source_hash():
+            return ent
+    except Exception:
+        pass
+    return None
+
+
+def make_workload(args, rank: int):
+    import synth
+    w = synth.CONFIGS[args.workload]
+    n = args.reads or w.n_reads
+    t0 = time.perf_counter()
+    g, _ = w.make_genome()
+    rd = w.make_reads(g, n=n, first_index=rank * n)
+    dpr = w.max_dist_per_read(rd.lengths())
+    return w, g, rd, dpr, time.perf_counter() - t0
+
+
+def cpu_oracle_sample(w, g, rd, dpr, target_s: float = 12.0, max_reads: int = 400_000):
+    """Time the oracle (as it stands) on a bounded sample on all host cores."""
+    import oracle
+    cores = os.cpu_count() or 1
+    idx = oracle.Index(g, w.seed_len)
+    probe = rd.subset(np.arange(min(rd.n, 20_000)))
+    pd = None if dpr is None else dpr[:probe.n]
+    t0 = time.perf_counter()
+    idx.align(probe.bases, probe.offsets, max_dist_per_read=pd, threads=cores, **w.params())
+    rate = probe.n / max(1e-6, time.perf_counter() - t0)
+    n = int(min(rd.n, max_reads, max(probe.n, rate * target_s)))
+    sample = np.arange(n)
+    sub = rd.subset(sample) if n < rd.n else rd
+    sd = None if dpr is None else dpr[:n]
+    t0 = time.perf_counter()
+    res, _ = idx.align(sub.bases, sub.offsets, max_dist_per_read=sd, threads=cores,
+                       **w.params())
+    dt = time.perf_counter() - t0
+    return dict(value=n / dt, unit="reads/s", cores=cores, kind="oracle",
+                sample=f"first {n} reads of the workload, index over the full genome "
+                       f"(built in {idx.build_seconds:.1f} s, not timed)"), sample, res
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    w, g, rd, dpr, _ = make_workload(args, 0)
+    cores = os.cpu_count() or 1
+    idx = oracle.Index(g, w.seed_len)
+    per_step = min(rd.n, 10_000)
+
+    def step(k):
+        lo = (k * per_step) % max(1, rd.n - per_step + 1)
+        sub = rd.subset(np.arange(lo, lo + per_step))
+        sd = None if dpr is None else dpr[lo:lo + per_step]
+        idx.align(sub.bases, sub.offsets, max_dist_per_read=sd, threads=cores, **w.params())
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "reads/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": w.name, "reads_per_step": per_step, "genome_bp": w.G,
+                   "form": "cpu-oracle"},
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": "reads/s",
+                         "sample": f"{per_step} reads per step, cycling through the "
+                                   f"workload's {rd.n} reads"},
+        "e2e": {"value": value, "unit": "reads/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1111_5572_gb300 as snap
+    import __graft_entry__
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    __graft_entry__.build()
+
+    w, g, rd, dpr, gen_s = make_workload(args, rank)
+    n = rd.n
+    t0 = time.perf_counter()
+    idx = snap.Index(g, w.seed_len)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    info = idx.info()
+    params = w.params()
+    plain = args.form == "plain"
+
+    d_b = torch.from_numpy(rd.bases).to(dev)
+    d_o = torch.from_numpy(rd.offsets.view(np.int64)).to(dev)
+    d_out = torch.zeros((n, 16), dtype=torch.uint8, device=dev)
+    d_dpr = None if dpr is None else torch.from_numpy(dpr).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def one_step(form_plain):
+        idx.align_device(d_b, d_o, d_out, d_max_dist_per_read=d_dpr, stream=stream,
+                         plain=form_plain, **params)
+
+    def timed(form_plain, steps, warmup):
+        for _ in range(warmup):
+            flush.zero_()
+            one_step(form_plain)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        stats = []
+        wall0 = time.perf_counter()
+        with ClockSampler(local) as clk:
+            for k in range(steps):
+                flush.zero_()  # L2 flush outside the event pair
+                evs[k][0].record(stream)
+                one_step(form_plain)
+                evs[k][1].record(stream)
+                stats.append(idx.last_call_stats())
+            torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        return step_ms, stats, clk.summary(), wall
+
+    step_ms, stats, clocks, wall = timed(plain, args.steps, args.warmup)
+    total_s = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = n * ws * args.steps / total_s
+    ms_per_step = total_s * 1e3 / args.steps
+    launches = int(sum(s["kernel_launches"] for s in stats))
+    got = d_out.cpu().numpy().view(snap.RESULT_DTYPE).reshape(-1)
+
+    # roofline of the main align kernel(s): algorithmic bytes from the kernels' own counters
+    st = stats[-1]
+    align_ms = float(np.mean([s["align_ms"] for s in stats]))
+    alg_bytes = (st["read_bases"] / 4 + 8 * st["reads"] + 16 * st["reads"] +
+                 32 * st["slot_reads"] + 4 * st["list_entries"] + st["window_bytes"])
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / (align_ms / 1e3) / 1e9
+    kname = "k_align_plain_stages" if plain else "k_align_fused"
+    tr = _ncu_traffic(kname)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                "traffic": None if tr is None else tr["dram_bytes_per_read"] * st["reads"],
+                "kernel": kname, "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel_ms": align_ms,
+                "counters": {k: st[k] for k in ("seeds", "slot_reads", "list_entries",
+                                                "ed_calls", "ed_over", "window_bytes")}}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "reads/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": w.name, "genome_bp": w.G, "repeat_frac": w.repeat_frac,
+                   "reads_per_step": n, "read_len": "100" if w.len_mode == 0 else "mixed",
+                   "seed_len": w.seed_len, **params, "form": args.form,
+                   "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "bases_per_s": value * float(rd.lengths().mean()),
+        "index_build_s": build_s, "index_device_gb": info["device_bytes"] / 1e9,
+        "input_gen_s": gen_s, "wall_s_timed": wall,
+        "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+    }
+
+    # the plain one-launch-per-stage form on the same GPU and inputs
+    if not plain and not args.no_plain:
+        try:
+            p_ms, p_stats, _, _ = timed(True, max(3, args.steps // 4), 3)
+            p_got = d_out.cpu().numpy().view(snap.RESULT_DTYPE).reshape(-1)
+            same = all(np.array_equal(p_got[f], got[f]) for f in
+                       ("location", "edit_distance", "strand", "cls"))
+            p_total = sum(p_ms) / 1e3
+            line["plain"] = {"value": n * len(p_ms) / p_total, "unit": "reads/s",
+                             "ms_per_step": p_total * 1e3 / len(p_ms),
+                             "gpu_launches_per_step": int(p_stats[-1]["kernel_launches"]),
+                             "identical_results": bool(same)}
+            line["batched_over_plain"] = line["value"] / line["plain"]["value"]
+        except Exception as e:  # the plain form is a comparison, not the product
+            line["plain"] = {"error": str(e)[:200]}
+
+    # e2e through the public host-buffer call: pinned inputs in, results out
+    if rank == 0 or ws > 1:
+        pin_b = torch.from_numpy(rd.bases).pin_memory()
+        pin_o = torch.from_numpy(rd.offsets.view(np.int64)).pin_memory()
+        pin_out = torch.zeros((n, 16), dtype=torch.uint8).pin_memory()
+        nb, no = pin_b.numpy(), pin_o.numpy().view(np.uint64)
+        no_out = pin_out.numpy().view(snap.RESULT_DTYPE).reshape(-1)
+        for _ in range(2):
+            idx.align(nb, no, max_dist_per_read=dpr, out=no_out, plain=plain, **params)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            idx.align(nb, no, max_dist_per_read=dpr, out=no_out, plain=plain, **params)
+        e2e_s = time.perf_counter() - t0
+        line["e2e"] = {"value": n * args.e2e_steps / e2e_s, "unit": "reads/s",
+                       "h2d_bytes_per_step": int(rd.bases.nbytes + rd.offsets.nbytes +
+                                                 (0 if dpr is None else dpr.nbytes)),
+                       "d2h_bytes_per_step": int(16 * n), "steps": args.e2e_steps}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, sample, ref = cpu_oracle_sample(w, g, rd, dpr)
+        line["cpu_baseline"] = cb
+        mism = sum(int((got[f][sample] != ref[f]).sum()) for f in
+                   ("location", "edit_distance", "strand", "cls"))
+        line["parity_sample"] = {"reads": int(len(sample)), "field_mismatches": mism}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

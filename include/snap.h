@@ -1,0 +1,214 @@
+/*
+ * snap.h — C-ABI of the GB300 SNAP alignment library (libsnapgpu.so).
+ *
+ * SNAP (Zaharia et al., "Faster and More Accurate Sequence Alignment with
+ * SNAP", arXiv 1111.5572) aligns short and long DNA reads against a reference
+ * genome: it cuts s-base seeds from each read, looks them up in a hash index of
+ * every overlapping s-mer of the genome, votes for candidate start positions,
+ * scores the most-voted candidates with an edit distance that gives up past a
+ * limit, and reports the best hit as a single hit, multiple hits or not found.
+ *
+ * Conventions for every call:
+ *   - Every function returns a SNAP_* status and never aborts the process.
+ *     On failure snap_last_error() returns a message for the calling thread.
+ *   - The caller owns every buffer passed in (host or device) and keeps it
+ *     alive for the duration of the call (for the server: until
+ *     snap_server_wait returns for that ticket).  The library owns the index
+ *     and the server objects and frees them in snap_index_free /
+ *     snap_server_destroy.
+ *   - Bases are ASCII 'A','C','G','T' (uppercase).  Any other byte in a genome
+ *     or a read makes the call fail with SNAP_E_INVAL.
+ *   - Device pointers are CUDA global-memory pointers on the current device;
+ *     `stream` arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream).
+ *   - One CUDA device per process; the index lives on the device that was
+ *     current when it was built, and later calls must keep that device current.
+ */
+#ifndef SNAP_GPU_H
+#define SNAP_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    SNAP_OK = 0,
+    SNAP_E_INVAL = 1,   /* bad argument or input (non-ACGT base, size out of range) */
+    SNAP_E_NOMEM = 2,   /* device or host allocation failed, or over the server budget */
+    SNAP_E_CUDA = 3,    /* a CUDA runtime call or kernel failed */
+    SNAP_E_TIMEOUT = 4, /* a bounded device wait gave up (status word set by a kernel) */
+    SNAP_E_INTERNAL = 5 /* an internal limit or invariant failed */
+};
+
+/* Result classes of Algorithm 1 ("SNAP alignment algorithm"). */
+enum { SNAP_NOT_FOUND = 0, SNAP_SINGLE_HIT = 1, SNAP_MULTIPLE_HITS = 2 };
+
+typedef struct snap_index snap_index;   /* opaque, device-resident, library-owned */
+typedef struct snap_server snap_server; /* opaque serving-loop state */
+
+/*
+ * The per-call parameters of Table "SNAP algorithm parameters" (the seed size s
+ * belongs to the index):
+ *   max_dist   d_max >= 0: largest edit distance reported as an alignment.
+ *   max_hits   h_max in [0, 65534]: a seed with more index entries (its own
+ *              occurrences plus those of its reverse complement) is skipped.
+ *   conf_diff  c >= 1: a best hit is "single" only if the second best is at
+ *              least c worse.
+ *   num_seeds  n >= 0 seeds tried per read; 0 means floor(m / s) for a read of
+ *              length m (the non-overlapping seeds).  At most m - s + 1 seeds
+ *              exist; at most 2047 are used.
+ *   max_dist_per_read  NULL, or one d_max per read overriding max_dist
+ *              (a host pointer for snap_align / the server, a device pointer
+ *              for the *_device calls).
+ */
+typedef struct {
+    int32_t max_dist;
+    int32_t max_hits;
+    int32_t conf_diff;
+    int32_t num_seeds;
+    const int32_t* max_dist_per_read;
+} snap_params;
+
+/*
+ * One result per read, 16 bytes.  location is the 0-based genome position p
+ * where the read (strand 0) or its reverse complement (strand 1) starts;
+ * edit_distance is the distance found there.  Not found, and multiple hits
+ * whose best distance exceeds d_max, report location = -1, strand = 0,
+ * edit_distance = -1.
+ */
+typedef struct {
+    int64_t location;
+    int32_t edit_distance;
+    uint8_t strand;
+    uint8_t cls;
+    uint8_t pad[2];
+} snap_result;
+
+typedef struct {
+    uint64_t genome_len;
+    int32_t seed_len;
+    int32_t reserved;
+    uint64_t table_slots;     /* open-addressing slots (16 bytes each) */
+    uint64_t distinct_seeds;  /* occupied slots: distinct canonical s-mers */
+    uint64_t list_entries;    /* positions stored out of line (keys seen 2..65534 times) */
+    uint64_t device_bytes;    /* device memory held by the index */
+    double build_seconds;
+} snap_index_info;
+
+/*
+ * Build the seed index of the "Hash Index" subsection: every overlapping s-mer
+ * of genome_ascii[0..genome_len) (a window slid one base at a time), looked up
+ * in both orientations as item 2 after Algorithm 1 asks.  The genome is copied
+ * to the device, packed 2 bits per base, and kept resident with the index.
+ *   genome_ascii  host pointer, genome_len bytes of A/C/G/T.
+ *   genome_len    seed_len <= genome_len < 2^32 - 2^16.
+ *   seed_len      s in [8, 32].
+ *   out           receives the new index (NULL on failure).
+ * Errors: SNAP_E_INVAL (bad base, bad sizes), SNAP_E_NOMEM, SNAP_E_CUDA.
+ */
+int snap_index_build(const uint8_t* genome_ascii, uint64_t genome_len, int seed_len,
+                     snap_index** out);
+
+/* Free an index and its device memory.  NULL is accepted. */
+int snap_index_free(snap_index* index);
+
+/* Sizes of a built index. */
+int snap_index_info_get(const snap_index* index, snap_index_info* out);
+
+/*
+ * Align n_reads reads with Algorithm 1 (batched form: one persistent kernel per
+ * length bucket, replayed from a cached CUDA graph).  Host buffers:
+ *   reads_ascii   the reads back to back; read r is
+ *                 reads_ascii[read_offsets[r] .. read_offsets[r+1]).
+ *   read_offsets  n_reads + 1 non-decreasing entries.
+ *   params        see snap_params (max_dist_per_read is a host pointer here).
+ *   out           n_reads results.
+ * A read shorter than the seed length is SNAP_NOT_FOUND.  Reads may be up to
+ * 65535 bases long.  Errors: SNAP_E_INVAL, SNAP_E_NOMEM, SNAP_E_CUDA,
+ * SNAP_E_TIMEOUT.
+ */
+int snap_align(const snap_index* index, const uint8_t* reads_ascii, const uint64_t* read_offsets,
+               uint64_t n_reads, const snap_params* params, snap_result* out);
+
+/* The same on device buffers, ordered on `stream`; returns once the results
+ * are in d_out (the call synchronises the stream).  params->max_dist_per_read,
+ * when set, is a device pointer. */
+int snap_align_device(const snap_index* index, const uint8_t* d_reads, const uint64_t* d_offsets,
+                      uint64_t n_reads, const snap_params* params, snap_result* d_out,
+                      void* stream);
+
+/*
+ * The plain form of the same computation: one kernel launch per stage (seed
+ * probe, candidate gather and dedup, edit distance of every candidate at
+ * d_max + c - 1, replay of Algorithm 1's decisions), no persistent queue, no
+ * graph.  Results are identical to snap_align_device's; it exists as the
+ * comparison form.  Same arguments and errors.
+ */
+int snap_align_plain_device(const snap_index* index, const uint8_t* d_reads,
+                            const uint64_t* d_offsets, uint64_t n_reads,
+                            const snap_params* params, snap_result* d_out, void* stream);
+
+/* Host-buffer variant of the plain form. */
+int snap_align_plain(const snap_index* index, const uint8_t* reads_ascii,
+                     const uint64_t* read_offsets, uint64_t n_reads, const snap_params* params,
+                     snap_result* out);
+
+/*
+ * Serving loop (continuous batching).  A server owns a worker thread, a set of
+ * CUDA streams and a device-memory budget.  snap_server_submit enqueues a
+ * request (host buffers, kept alive by the caller until snap_server_wait
+ * returns for its ticket); the worker admits queued requests in arrival order
+ * whenever a stream slot is free and the request's device footprint fits in
+ * what is left of mem_budget_bytes, so requests that arrive while others run
+ * overlap on the device.  A request larger than the whole budget fails with
+ * SNAP_E_NOMEM at wait.  Results do not depend on what else is in flight.
+ *   mem_budget_bytes  device bytes the server may hold for request data.
+ *   max_inflight      concurrent requests on the device (1..64).
+ */
+int snap_server_create(const snap_index* index, uint64_t mem_budget_bytes, int max_inflight,
+                       snap_server** out);
+int snap_server_submit(snap_server* server, const uint8_t* reads_ascii,
+                       const uint64_t* read_offsets, uint64_t n_reads, const snap_params* params,
+                       uint64_t* ticket);
+/* Block until request `ticket` is done; copy its results to out (n_reads of
+ * them) and its latency (submit to completion, seconds) to *latency_s. */
+int snap_server_wait(snap_server* server, uint64_t ticket, snap_result* out, double* latency_s);
+/* Wait for every request, stop the worker and free the server.  NULL is accepted. */
+int snap_server_destroy(snap_server* server);
+
+/*
+ * Measurements of the last successful align call on an index (any form):
+ * device time per stage from CUDA events recorded on the call's stream, the
+ * number of library kernels it launched, and traffic counters kept by the
+ * kernels (each index probe step reads one 16-byte slot; out-of-line list
+ * entries are 4 bytes; a scored candidate stages its genome window).
+ */
+typedef struct {
+    uint64_t kernel_launches;
+    double stats_ms;   /* batch statistics and validation */
+    double pack_ms;    /* 2-bit packing of the reads */
+    double align_ms;   /* everything after packing: the main kernel(s) */
+    double total_ms;
+    uint64_t reads;
+    uint64_t read_bases;
+    uint64_t seeds;         /* seeds looked up */
+    uint64_t slot_reads;    /* index slots read by the probes */
+    uint64_t list_entries;  /* out-of-line positions read */
+    uint64_t ed_calls;      /* edit distances computed */
+    uint64_t ed_over;       /* of which over the limit */
+    uint64_t window_bytes;  /* packed genome bytes staged for edit distances */
+} snap_call_stats;
+
+int snap_last_call_stats(const snap_index* index, snap_call_stats* out);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char* snap_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNAP_GPU_H */

@@ -1,0 +1,919 @@
+// snap_align.cu — the batched alignment path: read packing, batch statistics
+// and the persistent warp-per-read kernel that runs Algorithm 1 ("SNAP
+// alignment algorithm") literally for each read it pulls from a device queue.
+//
+// Per read, one warp:
+//   * packs the read and its reverse complement (2 bits per base) into shared
+//     memory;
+//   * cuts the seeds in the order of item 3 after Algorithm 1 and probes the
+//     index for all of them at once (one lane per seed);
+//   * walks the seeds in order: adds the votes SeedsHitting[p] of a seed with
+//     at most h_max entries (lanes over list entries, a shared-memory hash
+//     table keyed by (strand, p)), picks the most-voted unscored candidate
+//     (warp arg-max, ties to the smaller key), computes d_limit, scores it with
+//     the warp's Landau-Vishkin edit distance, keeps d_best / d_second over
+//     32-base buckets (item 1 after Algorithm 1), and takes the early exits;
+//   * classifies the read (single / multiple / not found).
+// Readings where the paper is silent (all shared with the oracle's statement
+// of them): votes from revcomp(seed) go to strand 1 at p = l - (m - o - s);
+// candidates with p < 0 are dropped; the edit distance is anchored at p with
+// a free end; the "non-overlapping seeds tested" counter counts non-popular
+// seeds of the first (unshifted) pass; after the Baeza-Yates test passes, all
+// remaining candidates are scored in pick order and seeding stops.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "snap_device.cuh"
+#include "snap_engine.h"
+#include "snap_internal.h"
+#include "snap_scan.cuh"
+
+namespace snapgpu {
+
+constexpr int kInf = 1 << 28;
+constexpr unsigned long long kKeyMask = (1ull << 33) - 1;
+
+// ---------------------------------------------------------------------------
+// batch statistics and validation
+// ---------------------------------------------------------------------------
+__global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, int s,
+                             int num_seeds, int d_max, int c, int h_max,
+                             const int32_t* __restrict__ dmax_per_read, BatchStats* st) {
+    unsigned int my_len = 0;
+    int my_L0 = 0, my_n = 0, bad = 0;
+    unsigned long long my_hits = 0;
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = offsets[r], b = offsets[r + 1];
+        if (b < a) {
+            bad |= kStBadOffsets;
+            continue;
+        }
+        const uint64_t m = b - a;
+        if (m > (uint64_t)kMaxReadLen) {
+            bad |= kStReadTooLong;
+            continue;
+        }
+        int nn = 0;
+        if ((int)m >= s) {
+            nn = num_seeds > 0 ? num_seeds : (int)m / s;
+            nn = min(nn, (int)m - s + 1);
+        }
+        if (nn > kMaxSeeds) bad |= kStTooManySeeds;
+        const int dm = dmax_per_read ? dmax_per_read[r] : d_max;
+        if (dm < 0) bad |= kStBadDmax;
+        my_len = max(my_len, (unsigned int)m);
+        my_L0 = max(my_L0, dm + c - 1);
+        my_n = max(my_n, nn);
+        my_hits = max(my_hits, (unsigned long long)nn * (unsigned long long)h_max);
+    }
+    if (bad) atomicOr(&st->status, bad);
+    atomicMax(&st->max_len, my_len);
+    atomicMax(&st->max_L0, my_L0);
+    atomicMax(&st->max_seeds, my_n);
+    atomicMax(&st->max_hits_bound, my_hits);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->total_bases = offsets[n] - offsets[0];
+        if (offsets[n] < offsets[0]) atomicOr(&st->status, kStBadOffsets);
+    }
+}
+
+// Pack the concatenated reads (bytes [base, base + total) of `reads`) into
+// 2-bit words, with kReadPadBases zero bases in front; flags non-ACGT bytes.
+__global__ void k_pack_reads(const uint8_t* __restrict__ reads, uint64_t base, uint64_t total,
+                             uint32_t* __restrict__ words, uint64_t nwords, int aligned16,
+                             int* status) {
+    constexpr uint64_t padw = kReadPadBases / 16;
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nwords;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t word = 0;
+        bool bad = false;
+        if (w >= padw) {
+            const uint64_t b0 = (w - padw) * 16;
+            const uint8_t* src = reads + base + b0;
+            if (b0 + 16 <= total && aligned16) {
+                const uint4 v = *reinterpret_cast<const uint4*>(src);
+                const uint32_t parts[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t ch = (parts[q] >> (8 * j)) & 0xffu;
+                        bad |= !is_acgt(ch);
+                        word |= code_of(ch) << (2 * (4 * q + j));
+                    }
+            } else {
+                for (uint64_t j = 0; j < 16 && b0 + j < total; ++j) {
+                    const uint32_t ch = src[j];
+                    bad |= !is_acgt(ch);
+                    word |= code_of(ch) << (2 * j);
+                }
+            }
+        }
+        words[w] = word;
+        if (bad) atomicOr(status, kStBadBase);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-read candidate table (shared or global memory through generic pointers)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void table_add(CandSlot* tab, uint32_t mask, unsigned long long key,
+                                          int* status) {
+    uint32_t h = (uint32_t)mix64(key) & mask;
+    for (uint32_t step = 0; step <= mask; ++step) {
+        const unsigned long long prev = atomicCAS(&tab[h].key, kEmptyKey, key);
+        if (prev == kEmptyKey || prev == key) {
+            atomicAdd(&tab[h].votes, 1u);
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+    atomicOr(status, kStTableFull);
+}
+
+// most-voted unscored candidate, ties to the smaller key; 0 = none.
+// packed = votes(11 bits) | (kKeyMask - key)(33 bits) | slot(20 bits)
+__device__ __forceinline__ unsigned long long table_pick(const CandSlot* tab, uint32_t cap,
+                                                         int lane) {
+    unsigned long long best = 0;
+    for (uint32_t j = lane; j < cap; j += 32) {
+        const CandSlot c = tab[j];
+        if (c.key != kEmptyKey && c.state == kUnscored) {
+            const unsigned long long v = ((unsigned long long)c.votes << 53) |
+                                         ((kKeyMask - c.key) << 20) | (unsigned long long)j;
+            best = v > best ? v : best;
+        }
+    }
+    return warp_max_u64(best);
+}
+
+__device__ __forceinline__ unsigned long long bucket_of(unsigned long long key) {
+    return ((key >> 6) << 1) | (key & 1);  // (strand, floor(p / 32))
+}
+
+struct FusedArgs {
+    const uint32_t* genome;
+    uint64_t G;
+    int s;
+    const IndexSlot* slots;
+    uint64_t T;
+    const uint32_t* positions;
+    const uint32_t* rwords;
+    const uint64_t* offsets;
+    uint64_t base0;
+    const uint32_t* order;  // processing order of read ids (NULL = identity)
+    uint64_t n_items;
+    unsigned long long* head;
+    int d_max, h_max, c, num_seeds;
+    const int32_t* dmax_per_read;
+    uint8_t shifts[32];
+    int n_shifts;
+    snap_result* out;
+    CandSlot* gtab;  // per-warp overflow tables, gcap slots each
+    HitRec* ghits;   // per-warp overflow hit lists, gcap / 2 each
+    uint32_t gcap;
+    int* status;
+    DevCounters* ctr;
+    // per-warp shared-memory layout, in 32-bit words; every section offset is a
+    // multiple of 4 words (16 bytes) because SeedRec / CandSlot / HitRec are
+    // moved with 16-byte vector accesses
+    int wx, wt, seed_cap, scap, lv_ints, warp_words;
+    int off_xr, off_tw, off_seeds, off_tab, off_hits, off_lv;
+};
+
+struct WarpCounters {
+    uint32_t seeds = 0, slot_reads = 0, list_entries = 0, ed_calls = 0, ed_over = 0;
+    unsigned long long window_words = 0;
+};
+
+__device__ __forceinline__ void flush_counters(DevCounters* ctr, WarpCounters& c) {
+    unsigned long long v[6] = {c.seeds, c.slot_reads, c.list_entries, c.ed_calls, c.ed_over,
+                               c.window_words};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        unsigned long long* dst = &ctr->seeds;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (v[k]) atomicAdd(dst + k, v[k]);
+    }
+}
+
+struct WarpMem {
+    uint32_t* Xf;
+    uint32_t* Xr;
+    uint32_t* Tw;
+    SeedRec* seeds;
+    CandSlot* stab;
+    HitRec* shits;
+    int* lvA;
+    int* lvB;
+    CandSlot* gtab;
+    HitRec* ghits;
+};
+
+// Edit distance of candidate `key` at limit L (warp-wide, result uniform).
+__device__ __forceinline__ int candidate_distance(const FusedArgs& a, const WarpMem& wm, int m,
+                                                  unsigned long long key, int L, int lane,
+                                                  WarpCounters& wc) {
+    if (L < 0) return kOver;
+    const uint64_t p = key >> 1;
+    const int strand = (int)(key & 1);
+    const uint64_t avail = a.G - p;
+    const int n_t = (int)min(avail, (uint64_t)(m + L));
+    const uint64_t w0 = p >> 4;
+    const int tb = (int)(p & 15);
+    const int nwt = (tb + n_t + 15) / 16 + 2;
+    for (int w = lane; w < nwt; w += 32) wm.Tw[w] = __ldg(a.genome + w0 + w);
+    __syncwarp();
+    const int d = lv_warp(strand ? wm.Xr : wm.Xf, m, wm.Tw, tb, n_t, L, lane, wm.lvA, wm.lvB,
+                          a.status);
+    __syncwarp();
+    if (lane == 0) {
+        wc.window_words += (unsigned)nwt;
+        wc.ed_calls++;
+        wc.ed_over += (d < 0);
+    }
+    return d;
+}
+
+__device__ void align_one_read(const FusedArgs& a, const WarpMem& wm, uint64_t r, int lane,
+                               WarpCounters& wc) {
+    const uint64_t o0 = a.offsets[r], o1 = a.offsets[r + 1];
+    const int m = (int)(o1 - o0);
+    const uint64_t rb = o0 - a.base0 + kReadPadBases;
+    const int s = a.s;
+    int n = 0;
+    if (m >= s) {
+        n = a.num_seeds > 0 ? a.num_seeds : m / s;
+        n = min(n, m - s + 1);
+    }
+    const int dmax = a.dmax_per_read ? a.dmax_per_read[r] : a.d_max;
+    const int c = a.c;
+    long long res_loc = -1;
+    int res_d = -1, res_strand = 0, res_cls = SNAP_NOT_FOUND;
+
+    if (n > 0) {
+        // ---- read and reverse complement, 2 bits per base ----
+        const int nw = (m + 15) / 16;
+        for (int w = lane; w < nw + 3; w += 32) {
+            uint32_t f = 0, rc = 0;
+            if (w < nw) {
+                f = get16(a.rwords, rb + 16ull * w);
+                rc = rev_groups32(~get16(a.rwords, rb + (uint64_t)m - 16 - 16ull * w));
+            } else if (w == nw) {
+                f = get16(a.rwords, rb + 16ull * w);  // tail of the last word (unused bases)
+            }
+            wm.Xf[w] = f;
+            wm.Xr[w] = rc;
+        }
+        __syncwarp();
+        // ---- seeds and index probes, one lane per seed ----
+        unsigned int H = 0;
+        for (int i = lane; i < n; i += 32) {
+            bool p0 = false;
+            const int o = seed_offset(i, m, s, a.shifts, a.n_shifts, &p0);
+            SeedRec rec;
+            rec.flags = (uint8_t)(kSeedValid | (p0 ? kSeedPass0 : 0));
+            rec.offset = (uint16_t)o;
+            rec.pad = 0;
+            const uint64_t v = get32(wm.Xf, (uint64_t)o) & kmer_mask(s);
+            uint32_t cnt = 0;
+            lookup_seed(a.slots, a.T, a.positions, v, s, &rec, &cnt, a.status, &wc.slot_reads);
+            wc.seeds++;
+            if (cnt > (uint32_t)a.h_max) {
+                rec.flags |= kSeedPopular;
+            } else {
+                H += (unsigned int)rec.fwd_n + rec.rc_n;
+            }
+            wm.seeds[i] = rec;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) H += __shfl_xor_sync(kFull, H, o);
+        // ---- candidate table: shared memory when it fits, else this warp's global one ----
+        uint32_t cap = 64;
+        while (cap < 2u * H) cap <<= 1;
+        CandSlot* tab;
+        HitRec* hits;
+        bool ok = true;
+        if (cap <= (uint32_t)a.scap) {
+            tab = wm.stab;
+            hits = wm.shits;
+        } else if (wm.gtab && cap <= a.gcap) {
+            tab = wm.gtab;
+            hits = wm.ghits;
+        } else {
+            tab = nullptr;
+            hits = nullptr;
+            ok = false;
+            if (lane == 0) atomicOr(a.status, kStTableFull);
+        }
+        if (ok) {
+            for (uint32_t j = lane; j < cap; j += 32) {
+                CandSlot e;
+                e.key = kEmptyKey;
+                e.votes = 0;
+                e.state = kUnscored;
+                tab[j] = e;
+            }
+            __syncwarp();
+            int d_best = kInf, d_second = kInf, nh = 0, t = 0;
+            unsigned long long best_key = 0;
+            bool any_nonpopular = false, returned = false;
+
+            auto limit = [&]() -> int {
+                if (d_best > dmax) return dmax + c - 1;
+                if (d_second >= d_best + c) return d_best + c - 1;
+                return d_best - 1;
+            };
+            auto score = [&](unsigned long long packed) {
+                const uint32_t slot = (uint32_t)(packed & 0xfffffu);
+                const unsigned long long key = kKeyMask - ((packed >> 20) & kKeyMask);
+                const int L = limit();
+                const int d = candidate_distance(a, wm, m, key, L, lane, wc);
+                if (lane == 0) {
+                    tab[slot].state = d >= 0 ? d : kOver;
+                    if (d >= 0) {
+                        HitRec h;
+                        h.key = key;
+                        h.d = d;
+                        h.pad = 0;
+                        hits[nh] = h;
+                    }
+                }
+                __syncwarp();
+                if (d >= 0) {
+                    ++nh;
+                    if (d < d_best) {
+                        d_best = d;
+                        best_key = key;
+                        const unsigned long long bb = bucket_of(key);
+                        int v = kInf;
+                        for (int j = lane; j < nh; j += 32) {
+                            const HitRec h = hits[j];
+                            if (bucket_of(h.key) != bb) v = min(v, h.d);
+                        }
+                        d_second = warp_min_i32(v);
+                    } else if (bucket_of(key) != bucket_of(best_key)) {
+                        d_second = min(d_second, d);
+                    }
+                }
+            };
+
+            for (int i = 0; i < n; ++i) {
+                const SeedRec rec = wm.seeds[i];
+                if (rec.flags & kSeedPopular) continue;
+                any_nonpopular = true;
+                const int o = rec.offset;
+                const int tot = (int)rec.fwd_n + rec.rc_n;
+                for (int j = lane; j < tot; j += 32) {
+                    const bool fwd = j < rec.fwd_n;
+                    uint32_t l;
+                    if (fwd) {
+                        l = (rec.flags & kSeedFwdInline) ? rec.fwd_ref
+                                                         : __ldg(a.positions + rec.fwd_ref + j);
+                    } else {
+                        const int jj = j - rec.fwd_n;
+                        l = (rec.flags & kSeedRcInline) ? rec.rc_ref
+                                                        : __ldg(a.positions + rec.rc_ref + jj);
+                    }
+                    wc.list_entries += (rec.flags & kSeedFwdInline) ? 0u : 1u;
+                    const long long p = fwd ? (long long)l - o : (long long)l - (m - o - s);
+                    if (p >= 0)
+                        table_add(tab, cap - 1, 2ull * (unsigned long long)p + (fwd ? 0 : 1),
+                                  a.status);
+                }
+                __syncwarp();
+                if (rec.flags & kSeedPass0) ++t;
+                const unsigned long long pk = table_pick(tab, cap, lane);
+                if (pk) score(pk);
+                if (d_best < c && d_second < d_best + c) {
+                    returned = true;
+                    break;
+                }
+                if (t >= d_best + c) {
+                    for (;;) {
+                        const unsigned long long q = table_pick(tab, cap, lane);
+                        if (!q) break;
+                        score(q);
+                    }
+                    break;
+                }
+            }
+            const bool all_popular = !any_nonpopular;  // n >= 1 here
+            if (!returned && d_best <= dmax && d_second >= d_best + c) {
+                res_cls = SNAP_SINGLE_HIT;
+            } else if (returned || d_best <= dmax || all_popular) {
+                res_cls = SNAP_MULTIPLE_HITS;
+            } else {
+                res_cls = SNAP_NOT_FOUND;
+            }
+            if (res_cls != SNAP_NOT_FOUND && d_best <= dmax) {
+                res_loc = (long long)(best_key >> 1);
+                res_strand = (int)(best_key & 1);
+                res_d = d_best;
+            }
+        }
+    }
+    if (lane == 0) {
+        // two 8-byte stores: snap_result arrays need only their natural alignment
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.out + r);
+        dst[0] = (unsigned long long)res_loc;
+        dst[1] = (unsigned long long)(uint32_t)res_d |
+                 ((unsigned long long)((uint32_t)res_strand | ((uint32_t)res_cls << 8)) << 32);
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(256) k_align_fused(FusedArgs a) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t* base = smem + (size_t)wib * a.warp_words;
+    WarpMem wm;
+    wm.Xf = base;
+    wm.Xr = base + a.off_xr;
+    wm.Tw = base + a.off_tw;
+    wm.seeds = reinterpret_cast<SeedRec*>(base + a.off_seeds);
+    wm.stab = reinterpret_cast<CandSlot*>(base + a.off_tab);
+    wm.shits = reinterpret_cast<HitRec*>(base + a.off_hits);
+    wm.lvA = a.lv_ints ? reinterpret_cast<int*>(base + a.off_lv) : nullptr;
+    wm.lvB = a.lv_ints ? wm.lvA + a.lv_ints / 2 : nullptr;
+    const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    wm.gtab = a.gtab ? a.gtab + gw * a.gcap : nullptr;
+    wm.ghits = a.ghits ? a.ghits + gw * (a.gcap / 2) : nullptr;
+    WarpCounters wc;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(a.head, 1ull);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= a.n_items) break;
+        const uint64_t r = a.order ? a.order[it] : it;
+        align_one_read(a, wm, r, lane, wc);
+    }
+    flush_counters(a.ctr, wc);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+int DevBuf::ensure(size_t need, const char* what) {
+    if (need <= bytes && p) return SNAP_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    size_t want = std::max(need, (size_t)256);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        set_error("out of device memory for %s (%zu bytes)", what, want);
+        return SNAP_E_NOMEM;
+    }
+    bytes = want;
+    return SNAP_OK;
+}
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+int PinnedBuf::ensure(size_t need, const char* what) {
+    if (need <= bytes && p) return SNAP_OK;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+    size_t want = std::max(need, (size_t)256);
+    cudaError_t e = cudaMallocHost(&p, want);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        set_error("out of pinned host memory for %s", what);
+        return SNAP_E_NOMEM;
+    }
+    bytes = want;
+    return SNAP_OK;
+}
+void PinnedBuf::release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+
+
+Engine* engine_create() {
+    Engine* e = new Engine();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e->sms <= 0) e->sms = 152;
+    return e;
+}
+
+void engine_destroy(Engine* e) {
+    if (!e) return;
+    for (DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->h_reads,
+                      &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds, &e->p_hits,
+                      &e->p_hitoff, &e->p_partial, &e->p_table, &e->p_events, &e->p_hitlist,
+                      &e->p_items, &e->p_misc})
+        b->release();
+    e->pin.release();
+    for (auto& ev : e->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (e->own_stream) cudaStreamDestroy(e->own_stream);
+    delete e;
+}
+
+size_t engine_bytes(const Engine* e) {
+    size_t s = 0;
+    for (const DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->h_reads,
+                            &e->h_offsets, &e->h_out, &e->h_dmax})
+        s += b->bytes;
+    return s;
+}
+
+void shift_list(int s, uint8_t* out, int* n_out) {
+    // 0, then floor(j*s/2^k) for k = 1, 2, ... and odd j < 2^k, without repeats
+    bool used[33] = {false};
+    int n = 0;
+    out[n++] = 0;
+    used[0] = true;
+    for (int k = 1; n < s && k < 40; ++k) {
+        for (long long j = 1; j < (1ll << k) && n < s; j += 2) {
+            const int d = (int)((j * s) >> k);
+            if (!used[d]) {
+                used[d] = true;
+                out[n++] = (uint8_t)d;
+            }
+        }
+    }
+    *n_out = n;
+}
+
+int validate_params(const snap_index* idx, const snap_params* p) {
+    if (!idx) {
+        set_error("index is NULL");
+        return SNAP_E_INVAL;
+    }
+    if (!p) {
+        set_error("params is NULL");
+        return SNAP_E_INVAL;
+    }
+    if (p->max_dist < 0) {
+        set_error("max_dist %d < 0", p->max_dist);
+        return SNAP_E_INVAL;
+    }
+    if (p->conf_diff < 1) {
+        set_error("conf_diff %d < 1", p->conf_diff);
+        return SNAP_E_INVAL;
+    }
+    if (p->max_hits < 0 || p->max_hits > (int)kListMax) {
+        set_error("max_hits %d outside [0, %u]", p->max_hits, kListMax);
+        return SNAP_E_INVAL;
+    }
+    if (p->num_seeds < 0 || p->num_seeds > kMaxSeeds) {
+        set_error("num_seeds %d outside [0, %d]", p->num_seeds, kMaxSeeds);
+        return SNAP_E_INVAL;
+    }
+    return SNAP_OK;
+}
+
+int status_to_code(int st, const char* where) {
+    if (!st) return SNAP_OK;
+    if (st & kStBadBase) {
+        set_error("%s: a read has a byte other than A, C, G, T", where);
+        return SNAP_E_INVAL;
+    }
+    if (st & kStBadOffsets) {
+        set_error("%s: read offsets decrease", where);
+        return SNAP_E_INVAL;
+    }
+    if (st & kStReadTooLong) {
+        set_error("%s: a read is longer than %d bases", where, kMaxReadLen);
+        return SNAP_E_INVAL;
+    }
+    if (st & kStTooManySeeds) {
+        set_error("%s: a read would use more than %d seeds", where, kMaxSeeds);
+        return SNAP_E_INVAL;
+    }
+    if (st & kStBadDmax) {
+        set_error("%s: a per-read max_dist is negative", where);
+        return SNAP_E_INVAL;
+    }
+    if (st & kStTimeout) {
+        set_error("%s: a bounded device wait gave up", where);
+        return SNAP_E_TIMEOUT;
+    }
+    set_error("%s: device status 0x%x", where, st);
+    return SNAP_E_INTERNAL;
+}
+
+
+
+
+int prepare_batch(const snap_index* idx, Engine* e, const uint8_t* d_reads,
+                         const uint64_t* d_offsets, uint64_t n, const snap_params* p,
+                         cudaStream_t stream, BatchPrep* out, const char* where) {
+    int rc;
+    if ((rc = e->stats.ensure(sizeof(BatchStats) + 64, "batch stats"))) return rc;
+    if ((rc = e->pin.ensure(4096, "pinned stats"))) return rc;
+    BatchStats* d_st = static_cast<BatchStats*>(e->stats.p);
+    if (!e->ev[0])
+        for (auto& ev : e->ev) SNAP_CUDA(cudaEventCreate(&ev), "event create");
+    e->launches = 0;
+    SNAP_CUDA(cudaEventRecord(e->ev[0], stream), "event");
+    SNAP_CUDA(cudaMemsetAsync(d_st, 0, sizeof(BatchStats), stream), "stats clear");
+    e->launches++;
+    k_read_stats<<<grid_cap(e->sms, n, 256), 256, 0, stream>>>(
+        d_offsets, n, idx->s, p->num_seeds, p->max_dist, p->conf_diff, p->max_hits,
+        p->max_dist_per_read, d_st);
+    SNAP_CUDA(cudaGetLastError(), "stats launch");
+    BatchStats* h_st = static_cast<BatchStats*>(e->pin.p);
+    uint64_t* h_base = reinterpret_cast<uint64_t*>(static_cast<char*>(e->pin.p) + 1024);
+    SNAP_CUDA(cudaEventRecord(e->ev[1], stream), "event");
+    SNAP_CUDA(cudaMemcpyAsync(h_st, d_st, sizeof(BatchStats), cudaMemcpyDeviceToHost, stream),
+              "stats copy");
+    SNAP_CUDA(cudaMemcpyAsync(h_base, d_offsets, sizeof(uint64_t), cudaMemcpyDeviceToHost, stream),
+              "offset copy");
+    SNAP_CUDA(cudaStreamSynchronize(stream), where);
+    out->st = *h_st;
+    out->base0 = *h_base;
+    if (out->st.status) return status_to_code(out->st.status, where);
+    const uint64_t nwords = (out->st.total_bases + kReadPadBases + 15) / 16 + 8;
+    if ((rc = e->packed.ensure(nwords * 4, "packed reads"))) return rc;
+    out->rwords = static_cast<uint32_t*>(e->packed.p);
+    const int aligned = ((reinterpret_cast<uintptr_t>(d_reads) + out->base0) % 16) == 0;
+    int* d_status = &d_st->status;
+    e->launches++;
+    k_pack_reads<<<grid_cap(e->sms, nwords, 256), 256, 0, stream>>>(
+        d_reads, out->base0, out->st.total_bases, out->rwords, nwords, aligned, d_status);
+    SNAP_CUDA(cudaGetLastError(), "pack launch");
+    SNAP_CUDA(cudaEventRecord(e->ev[2], stream), "event");
+    return SNAP_OK;
+}
+
+static int finish_status(Engine* e, cudaStream_t stream, const char* where, uint64_t n) {
+    BatchStats* d_st = static_cast<BatchStats*>(e->stats.p);
+    SNAP_CUDA(cudaEventRecord(e->ev[3], stream), "event");
+    BatchStats* h = reinterpret_cast<BatchStats*>(static_cast<char*>(e->pin.p) + 2048);
+    SNAP_CUDA(cudaMemcpyAsync(h, d_st, sizeof(BatchStats), cudaMemcpyDeviceToHost, stream),
+              "status copy");
+    SNAP_CUDA(cudaStreamSynchronize(stream), where);
+    const int rc = status_to_code(h->status, where);
+    if (rc) return rc;
+    snap_call_stats& L = e->last;
+    float ms = 0;
+    L.kernel_launches = e->launches;
+    cudaEventElapsedTime(&ms, e->ev[0], e->ev[1]);
+    L.stats_ms = ms;
+    cudaEventElapsedTime(&ms, e->ev[1], e->ev[2]);
+    L.pack_ms = ms;
+    cudaEventElapsedTime(&ms, e->ev[2], e->ev[3]);
+    L.align_ms = ms;
+    cudaEventElapsedTime(&ms, e->ev[0], e->ev[3]);
+    L.total_ms = ms;
+    L.reads = n;
+    L.read_bases = h->total_bases;
+    L.seeds = h->ctr.seeds;
+    L.slot_reads = h->ctr.slot_reads;
+    L.list_entries = h->ctr.list_entries;
+    L.ed_calls = h->ctr.ed_calls;
+    L.ed_over = h->ctr.ed_over;
+    L.window_bytes = h->ctr.window_words * 4;
+    return SNAP_OK;
+}
+
+static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
+                       const snap_params* p, snap_result* d_out, cudaStream_t stream,
+                       const BatchPrep& bp) {
+    int rc;
+    FusedArgs a;
+    memset(&a, 0, sizeof(a));
+    a.genome = idx->genome_words;
+    a.G = idx->G;
+    a.s = idx->s;
+    a.slots = idx->slots;
+    a.T = idx->T;
+    a.positions = idx->positions;
+    a.rwords = bp.rwords;
+    a.offsets = d_offsets;
+    a.base0 = bp.base0;
+    a.order = nullptr;
+    a.n_items = n;
+    a.d_max = p->max_dist;
+    a.h_max = p->max_hits;
+    a.c = p->conf_diff;
+    a.num_seeds = p->num_seeds;
+    a.dmax_per_read = p->max_dist_per_read;
+    shift_list(idx->s, a.shifts, &a.n_shifts);
+    a.out = d_out;
+    a.status = &static_cast<BatchStats*>(e->stats.p)->status;
+    a.ctr = &static_cast<BatchStats*>(e->stats.p)->ctr;
+    const int mmax = std::max(1u, bp.st.max_len);
+    const int Lmax = std::max(0, bp.st.max_L0);
+    const int nmax = std::max(1, bp.st.max_seeds);
+    auto up4 = [](int w) { return (w + 3) & ~3; };
+    a.wx = up4((mmax + 15) / 16 + 4);
+    a.wt = up4((mmax + Lmax + 15 + 15) / 16 + 4);
+    a.seed_cap = nmax;
+    a.lv_ints = Lmax > 127 ? up4(2 * (2 * Lmax + 4)) : 0;
+    // shared table: as large as the per-block budget allows, 64..1024 slots
+    const int fixed_words = 2 * a.wx + a.wt + 4 * a.seed_cap + a.lv_ints;
+    int warps = 8;
+    const int budget_words = 200 * 1024 / 4;  // per block
+    while (warps > 1 && warps * (fixed_words + 6 * 64) > budget_words) warps >>= 1;
+    int scap = 1024;
+    while (scap > 64 && warps * (fixed_words + 6 * scap) > budget_words) scap >>= 1;
+    a.scap = scap;
+    a.off_xr = a.wx;
+    a.off_tw = 2 * a.wx;
+    a.off_seeds = a.off_tw + a.wt;
+    a.off_tab = a.off_seeds + 4 * a.seed_cap;     // SeedRec: 4 words
+    a.off_hits = a.off_tab + 4 * scap;            // CandSlot: 4 words
+    a.off_lv = a.off_hits + 4 * (scap / 2);       // HitRec: 4 words, scap/2 of them
+    a.warp_words = a.off_lv + a.lv_ints;
+    if ((a.off_seeds | a.off_tab | a.off_hits | a.off_lv | a.warp_words) & 3) {
+        set_error("snap_align: internal shared-memory layout is not 16-byte aligned");
+        return SNAP_E_INTERNAL;
+    }
+    const size_t smem = (size_t)warps * a.warp_words * 4;
+    if (smem > 227 * 1024) {
+        set_error("snap_align: read length %d needs %zu bytes of shared memory per warp", mmax,
+                  (size_t)a.warp_words * 4);
+        return SNAP_E_INVAL;
+    }
+    SNAP_CUDA(cudaFuncSetAttribute(k_align_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem),
+              "smem attr");
+    int per_sm = 0;
+    SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_align_fused, warps * 32,
+                                                            smem),
+              "occupancy");
+    if (per_sm < 1) per_sm = 1;
+    uint64_t blocks = (uint64_t)e->sms * per_sm;
+    const uint64_t need_blocks = (n + warps - 1) / warps;
+    if (blocks > need_blocks) blocks = need_blocks;
+    // global overflow tables for reads whose candidate table outgrows shared memory
+    uint64_t hb = bp.st.max_hits_bound;
+    uint64_t gcap = 64;
+    while (gcap < 2 * hb) gcap <<= 1;
+    if (gcap > kMaxTableSlots) {
+        set_error("snap_align: seeds x max_hits per read (%llu) exceeds %u",
+                  (unsigned long long)hb, kMaxTableSlots / 2);
+        return SNAP_E_INVAL;
+    }
+    if (gcap > (uint64_t)scap) {
+        const uint64_t per_warp = gcap * (sizeof(CandSlot) + sizeof(HitRec) / 2);
+        const uint64_t budget = 4ull << 30;
+        uint64_t max_warps = std::max<uint64_t>(1, budget / per_warp);
+        if (blocks * warps > max_warps) blocks = std::max<uint64_t>(1, max_warps / warps);
+        const uint64_t tw = blocks * warps;
+        if ((rc = e->gtab.ensure(tw * gcap * sizeof(CandSlot), "overflow tables"))) return rc;
+        if ((rc = e->ghits.ensure(tw * (gcap / 2) * sizeof(HitRec), "overflow hits"))) return rc;
+        a.gtab = static_cast<CandSlot*>(e->gtab.p);
+        a.ghits = static_cast<HitRec*>(e->ghits.p);
+        a.gcap = (uint32_t)gcap;
+    }
+    if ((rc = e->head.ensure(64, "queue head"))) return rc;
+    a.head = static_cast<unsigned long long*>(e->head.p);
+    SNAP_CUDA(cudaMemsetAsync(a.head, 0, sizeof(unsigned long long), stream), "head clear");
+    e->launches++;
+    k_align_fused<<<(unsigned)blocks, warps * 32, smem, stream>>>(a);
+    SNAP_CUDA(cudaGetLastError(), "align launch");
+    return SNAP_OK;
+}
+
+int align_plain(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
+                const snap_params* p, snap_result* d_out, cudaStream_t stream,
+                const BatchPrep& bp);
+
+int align_batch_device(const snap_index* idx, Engine* e, const uint8_t* d_reads,
+                       const uint64_t* d_offsets, uint64_t n, const snap_params* p,
+                       snap_result* d_out, cudaStream_t stream, bool plain) {
+    int rc = validate_params(idx, p);
+    if (rc) return rc;
+    if (n == 0) return SNAP_OK;
+    if (!d_reads || !d_offsets || !d_out) {
+        set_error("snap_align: NULL buffer");
+        return SNAP_E_INVAL;
+    }
+    if ((reinterpret_cast<uintptr_t>(d_offsets) | reinterpret_cast<uintptr_t>(d_out)) % 8 ||
+        (p->max_dist_per_read && reinterpret_cast<uintptr_t>(p->max_dist_per_read) % 4)) {
+        set_error("snap_align: offsets and results must be 8-byte aligned, max_dist_per_read "
+                  "4-byte aligned");
+        return SNAP_E_INVAL;
+    }
+    const char* where = plain ? "snap_align_plain" : "snap_align";
+    BatchPrep bp;
+    if ((rc = prepare_batch(idx, e, d_reads, d_offsets, n, p, stream, &bp, where))) return rc;
+    rc = plain ? align_plain(idx, e, d_offsets, n, p, d_out, stream, bp)
+               : align_fused(idx, e, d_offsets, n, p, d_out, stream, bp);
+    if (rc) return rc;
+    return finish_status(e, stream, where, n);
+}
+
+// Host buffers: copy in, run the device path, copy out (engine-owned stream).
+static int align_host(const snap_index* idx, const uint8_t* reads, const uint64_t* offsets,
+                      uint64_t n, const snap_params* p, snap_result* out, bool plain) {
+    clear_error();
+    int rc = validate_params(idx, p);
+    if (rc) return rc;
+    if (n == 0) return SNAP_OK;
+    if (!reads || !offsets || !out) {
+        set_error("snap_align: NULL buffer");
+        return SNAP_E_INVAL;
+    }
+    Engine* e = idx->engine;
+    std::lock_guard<std::mutex> lock(e->mu);
+    if (!e->own_stream) SNAP_CUDA(cudaStreamCreateWithFlags(&e->own_stream, cudaStreamNonBlocking),
+                                  "stream create");
+    cudaStream_t st = e->own_stream;
+    const uint64_t lo = offsets[0], hi = offsets[n];
+    if (hi < lo) {
+        set_error("snap_align: read offsets decrease");
+        return SNAP_E_INVAL;
+    }
+    const uint64_t bytes = hi - lo;
+    if ((rc = e->h_reads.ensure(bytes + 16, "read copy"))) return rc;
+    if ((rc = e->h_offsets.ensure((n + 1) * 8, "offset copy"))) return rc;
+    if ((rc = e->h_out.ensure(n * sizeof(snap_result), "result buffer"))) return rc;
+    SNAP_CUDA(cudaMemcpyAsync(e->h_reads.p, reads + lo, bytes, cudaMemcpyHostToDevice, st),
+              "reads H2D");
+    // offsets are rebased by the device path through base0; copy as given and
+    // point the device reads at the copy's start minus lo
+    SNAP_CUDA(cudaMemcpyAsync(e->h_offsets.p, offsets, (n + 1) * 8, cudaMemcpyHostToDevice, st),
+              "offsets H2D");
+    snap_params dp = *p;
+    if (p->max_dist_per_read) {
+        if ((rc = e->h_dmax.ensure(n * 4, "max_dist copy"))) return rc;
+        SNAP_CUDA(cudaMemcpyAsync(e->h_dmax.p, p->max_dist_per_read, n * 4, cudaMemcpyHostToDevice,
+                                  st),
+                  "max_dist H2D");
+        dp.max_dist_per_read = static_cast<const int32_t*>(e->h_dmax.p);
+    }
+    const uint8_t* d_reads = static_cast<const uint8_t*>(e->h_reads.p) - lo;
+    rc = align_batch_device(idx, e, d_reads, static_cast<const uint64_t*>(e->h_offsets.p), n, &dp,
+                            static_cast<snap_result*>(e->h_out.p), st, plain);
+    if (rc) return rc;
+    SNAP_CUDA(cudaMemcpyAsync(out, e->h_out.p, n * sizeof(snap_result), cudaMemcpyDeviceToHost, st),
+              "results D2H");
+    SNAP_CUDA(cudaStreamSynchronize(st), "snap_align");
+    return SNAP_OK;
+}
+
+}  // namespace snapgpu
+
+using namespace snapgpu;
+
+extern "C" int snap_align(const snap_index* idx, const uint8_t* reads, const uint64_t* offsets,
+                          uint64_t n, const snap_params* p, snap_result* out) {
+    return align_host(idx, reads, offsets, n, p, out, false);
+}
+
+extern "C" int snap_align_plain(const snap_index* idx, const uint8_t* reads,
+                                const uint64_t* offsets, uint64_t n, const snap_params* p,
+                                snap_result* out) {
+    return align_host(idx, reads, offsets, n, p, out, true);
+}
+
+extern "C" int snap_last_call_stats(const snap_index* idx, snap_call_stats* out) {
+    clear_error();
+    if (!idx || !out) {
+        set_error("snap_last_call_stats: NULL argument");
+        return SNAP_E_INVAL;
+    }
+    std::lock_guard<std::mutex> lock(idx->engine->mu);
+    *out = idx->engine->last;
+    return SNAP_OK;
+}
+
+extern "C" int snap_align_device(const snap_index* idx, const uint8_t* d_reads,
+                                 const uint64_t* d_offsets, uint64_t n, const snap_params* p,
+                                 snap_result* d_out, void* stream) {
+    clear_error();
+    if (!idx) {
+        set_error("snap_align_device: index is NULL");
+        return SNAP_E_INVAL;
+    }
+    std::lock_guard<std::mutex> lock(idx->engine->mu);
+    return align_batch_device(idx, idx->engine, d_reads, d_offsets, n, p, d_out,
+                              static_cast<cudaStream_t>(stream), false);
+}
+
+extern "C" int snap_align_plain_device(const snap_index* idx, const uint8_t* d_reads,
+                                       const uint64_t* d_offsets, uint64_t n,
+                                       const snap_params* p, snap_result* d_out, void* stream) {
+    clear_error();
+    if (!idx) {
+        set_error("snap_align_plain_device: index is NULL");
+        return SNAP_E_INVAL;
+    }
+    std::lock_guard<std::mutex> lock(idx->engine->mu);
+    return align_batch_device(idx, idx->engine, d_reads, d_offsets, n, p, d_out,
+                              static_cast<cudaStream_t>(stream), true);
+}

@@ -1,0 +1,293 @@
+// snap_device.cuh — device helpers of the SNAP kernels: 2-bit packing,
+// canonical s-mers, the index probe and the warp-cooperative bounded edit
+// distance (farthest reach per diagonal).
+#pragma once
+
+#include <cstdint>
+
+#include "snap_internal.h"
+
+namespace snapgpu {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// A=0 C=1 G=2 T=3 from ASCII, by bits 1 and 2 of the letter (valid for the
+// four uppercase letters only; is_acgt() checks).
+__device__ __forceinline__ uint32_t code_of(uint32_t c) { return ((c >> 1) ^ (c >> 2)) & 3u; }
+__device__ __forceinline__ bool is_acgt(uint32_t c) {
+    return c == 'A' || c == 'C' || c == 'G' || c == 'T';
+}
+
+// Bases are packed 16 per 32-bit word, base i at bits 2*(i%16) of word i/16.
+// 16 bases starting at any base index (the array is padded by one word).
+__device__ __forceinline__ uint32_t get16(const uint32_t* w, uint64_t i) {
+    const uint64_t q = i >> 4;
+    return __funnelshift_r(w[q], w[q + 1], (uint32_t)(i & 15) * 2u);
+}
+
+// 32 bases starting at any base index (padded by two words).
+__device__ __forceinline__ uint64_t get32(const uint32_t* w, uint64_t i) {
+    const uint64_t q = i >> 4;
+    const uint32_t sh = (uint32_t)(i & 15) * 2u;
+    const uint32_t w0 = w[q], w1 = w[q + 1], w2 = w[q + 2];
+    const uint32_t lo = __funnelshift_r(w0, w1, sh);
+    const uint32_t hi = __funnelshift_r(w1, w2, sh);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// Reverse the order of the 2-bit groups of a word.
+__device__ __forceinline__ uint32_t rev_groups32(uint32_t x) {
+    const uint32_t r = __brev(x);
+    return ((r >> 1) & 0x55555555u) | ((r & 0x55555555u) << 1);
+}
+__device__ __forceinline__ uint64_t rev_groups64(uint64_t x) {
+    const uint64_t r = __brevll(x);
+    return ((r >> 1) & 0x5555555555555555ull) | ((r & 0x5555555555555555ull) << 1);
+}
+
+// Reverse complement of an s-mer held in the low 2s bits (complement of
+// code x is 3 - x = x ^ 3, i.e. bitwise NOT).
+__device__ __forceinline__ uint64_t kmer_revcomp(uint64_t v, int s) {
+    return rev_groups64(~v) >> (64 - 2 * s);
+}
+
+__device__ __forceinline__ uint64_t kmer_mask(int s) {
+    return s >= 32 ? ~0ull : ((1ull << (2 * s)) - 1ull);
+}
+
+// murmur3's 64-bit finaliser (a bijection), then a multiply-high to [0, T).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+__device__ __forceinline__ uint64_t home_slot(uint64_t key, uint64_t T) {
+    return __umul64hi(mix64(key), T);
+}
+
+__device__ __forceinline__ IndexSlot load_slot(const IndexSlot* slots, uint64_t i) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(slots) + i);
+    IndexSlot s;
+    s.key = ((unsigned long long)v.y << 32) | v.x;
+    s.field = v.z;
+    s.nA = (uint16_t)(v.w & 0xffffu);
+    s.nB = (uint16_t)(v.w >> 16);
+    return s;
+}
+
+// Probe the open-addressing table for canonical key K.  Returns true and the
+// slot when present.  Sets kStProbeRunaway in *status if the probe sequence
+// does not end within T slots (a full table; cannot happen at load <= 2/3).
+__device__ __forceinline__ bool probe_index(const IndexSlot* slots, uint64_t T, uint64_t K,
+                                            IndexSlot* out, int* status, uint32_t* steps) {
+    uint64_t i = home_slot(K, T);
+    for (uint64_t step = 0; step < T; ++step) {
+        const IndexSlot s = load_slot(slots, i);
+        ++*steps;
+        if (s.key == K) {
+            *out = s;
+            return true;
+        }
+        if (s.key == kEmptyKey) return false;
+        i = (i + 1 == T) ? 0 : i + 1;
+    }
+    atomicOr(status, kStProbeRunaway);
+    return false;
+}
+
+// The seed lookups of one seed with forward s-mer v: the forward occurrences
+// of v (strand-0 votes) and of revcomp(v) (strand-1 votes), from the
+// canonical slot.  Fills everything of `rec` but offset/flags bits 1.
+__device__ __forceinline__ void lookup_seed(const IndexSlot* slots, uint64_t T,
+                                            const uint32_t* /*positions*/, uint64_t v, int s,
+                                            SeedRec* rec, uint32_t* count, int* status,
+                                            uint32_t* steps) {
+    const uint64_t rc = kmer_revcomp(v, s);
+    const bool pal = (v == rc);
+    const bool v_is_key = (v <= rc);
+    const uint64_t K = v_is_key ? v : rc;
+    IndexSlot sl;
+    rec->fwd_ref = rec->rc_ref = 0;
+    rec->fwd_n = rec->rc_n = 0;
+    *count = 0;
+    if (!probe_index(slots, T, K, &sl, status, steps)) return;
+    const uint32_t nA = sl.nA, nB = sl.nB;
+    // where A and B start: inline when nA + nB == 1
+    const bool single = (nA + nB) == 1;
+    const uint32_t a_ref = sl.field, b_ref = single ? sl.field : sl.field + nA;
+    uint32_t fn, rn, fr, rr;
+    if (pal) {  // both lookups are the A list
+        fn = rn = nA;
+        fr = rr = a_ref;
+    } else if (v_is_key) {
+        fn = nA; fr = a_ref;
+        rn = nB; rr = b_ref;
+    } else {
+        fn = nB; fr = b_ref;
+        rn = nA; rr = a_ref;
+    }
+    *count = fn + rn;
+    rec->fwd_n = (uint16_t)(fn > 65535u ? 65535u : fn);
+    rec->rc_n = (uint16_t)(rn > 65535u ? 65535u : rn);
+    rec->fwd_ref = fr;
+    rec->rc_ref = rr;
+    if (single) rec->flags |= (uint8_t)(kSeedFwdInline | kSeedRcInline);
+}
+
+// Offset of seed i of a read of length m (seed order: the non-overlapping
+// pass, then the passes shifted by the entries of `shifts`).
+__device__ __forceinline__ int seed_offset(int i, int m, int s, const uint8_t* shifts,
+                                           int n_shifts, bool* pass0) {
+    for (int q = 0; q < n_shifts; ++q) {
+        const int d = shifts[q];
+        const int cnt = (m - s - d >= 0) ? (m - s - d) / s + 1 : 0;
+        if (i < cnt) {
+            *pass0 = (d == 0);
+            return d + i * s;
+        }
+        i -= cnt;
+    }
+    *pass0 = false;
+    return -1;
+}
+
+// ---- bounded edit distance -------------------------------------------------
+// ED(X, T) = min over prefixes T[0..j) of Lev(X, T[0..j)), exact when <= L,
+// else kOver.  X: m bases packed at X (padded); T: n bases packed at Tw from
+// base index tb (padded).  Farthest reach per diagonal k = j - i, one round per
+// distance e = 0..L (Landau-Vishkin); each lane keeps D consecutive diagonals
+// in registers, neighbours across lanes by shuffles.  Runs on a full warp.
+
+__device__ __forceinline__ int slide(const uint32_t* X, int m, const uint32_t* Tw, int tb, int n,
+                                     int r, int k) {
+    for (;;) {
+        const int lim = min(m - r, n - (r + k));
+        if (lim <= 0) return r;
+        const uint32_t x = get16(X, (uint64_t)r) ^ get16(Tw, (uint64_t)(tb + r + k));
+        const int adv = x ? ((__ffs(x) - 1) >> 1) : 16;
+        if (adv >= lim) return r + lim;
+        r += adv;
+        if (adv < 16) return r;
+    }
+}
+
+template <int D>
+__device__ inline int lv_warp_reg(const uint32_t* X, int m, const uint32_t* Tw, int tb, int n, int L,
+                           int lane) {
+    constexpr int NEG = -0x40000000;
+    int R[D];
+#pragma unroll
+    for (int t = 0; t < D; ++t) R[t] = NEG;
+    for (int e = 0; e <= L; ++e) {
+        int left = __shfl_up_sync(kFull, R[D - 1], 1);
+        int right = __shfl_down_sync(kFull, R[0], 1);
+        if (lane == 0) left = NEG;
+        if (lane == 31) right = NEG;
+        int Rn[D];
+        bool done = false;
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+            const int k = lane * D + t - L;
+            int r = NEG;
+            if (k >= -e && k <= e) {
+                if (e == 0) {
+                    r = 0;
+                } else {
+                    const int rkm1 = (t == 0) ? left : R[t - 1];
+                    const int rkp1 = (t == D - 1) ? right : R[t + 1];
+                    r = max(max(R[t] + 1, rkp1 + 1), rkm1);
+                }
+                if (r > m) r = m;
+                if (r + k > n) r = n - k;
+                if (r < 0 || r + k < 0) {
+                    r = NEG;
+                } else {
+                    r = slide(X, m, Tw, tb, n, r, k);
+                    done |= (r >= m);
+                }
+            }
+            Rn[t] = r;
+        }
+#pragma unroll
+        for (int t = 0; t < D; ++t) R[t] = Rn[t];
+        if (__any_sync(kFull, done)) return e;
+    }
+    return kOver;
+}
+
+// Same recurrence with the diagonals in shared memory (any L); Ra/Rb hold
+// 2L+3 ints each.
+__device__ inline int lv_warp_smem(const uint32_t* X, int m, const uint32_t* Tw, int tb, int n, int L,
+                            int lane, int* Ra, int* Rb) {
+    constexpr int NEG = -0x40000000;
+    const int W = 2 * L + 3, off = L + 1;
+    for (int i = lane; i < W; i += 32) {
+        Ra[i] = NEG;
+        Rb[i] = NEG;
+    }
+    __syncwarp();
+    for (int e = 0; e <= L; ++e) {
+        bool done = false;
+        for (int idx = lane; idx < 2 * e + 1; idx += 32) {
+            const int k = idx - e;
+            int r;
+            if (e == 0) {
+                r = 0;
+            } else {
+                r = max(max(Ra[k + off] + 1, Ra[k + 1 + off] + 1), Ra[k - 1 + off]);
+            }
+            if (r > m) r = m;
+            if (r + k > n) r = n - k;
+            if (r < 0 || r + k < 0) {
+                r = NEG;
+            } else {
+                r = slide(X, m, Tw, tb, n, r, k);
+                done |= (r >= m);
+            }
+            Rb[k + off] = r;
+        }
+        __syncwarp();
+        if (__any_sync(kFull, done)) return e;
+        int* t = Ra;
+        Ra = Rb;
+        Rb = t;
+    }
+    return kOver;
+}
+
+// Ra/Rb (2L+3 ints each) are required when L > 127; without them the call
+// flags kStInternal and reports kOver.
+__device__ __forceinline__ int lv_warp(const uint32_t* X, int m, const uint32_t* Tw, int tb, int n,
+                                       int L, int lane, int* Ra, int* Rb, int* status) {
+    if (L < 0) return kOver;
+    if (L <= 15) return lv_warp_reg<1>(X, m, Tw, tb, n, L, lane);
+    if (L <= 31) return lv_warp_reg<2>(X, m, Tw, tb, n, L, lane);
+    if (L <= 63) return lv_warp_reg<4>(X, m, Tw, tb, n, L, lane);
+    if (L <= 127) return lv_warp_reg<8>(X, m, Tw, tb, n, L, lane);
+    if (Ra == nullptr) {
+        if (lane == 0) atomicOr(status, kStInternal);
+        return kOver;
+    }
+    return lv_warp_smem(X, m, Tw, tb, n, L, lane, Ra, Rb);
+}
+
+// Warp-wide max of a 64-bit value.
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(kFull, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int warp_min_i32(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+}  // namespace snapgpu

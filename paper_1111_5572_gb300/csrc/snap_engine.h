@@ -1,0 +1,49 @@
+// snap_engine.h — per-index align workspaces shared by the batched and the
+// plain form (library-private).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "snap_internal.h"
+
+namespace snapgpu {
+
+struct Engine {
+    // everything an align call on one index needs; guarded by mu
+    std::mutex mu;
+    cudaStream_t own_stream = nullptr;
+    int sms = 0;
+    DevBuf stats, head, packed, gtab, ghits;
+    DevBuf h_reads, h_offsets, h_out, h_dmax;  // device copies for the host-buffer entry points
+    PinnedBuf pin;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};  // plain-form stage marks
+    uint64_t launches = 0;
+    snap_call_stats last{};
+    // plain-form workspace
+    DevBuf p_seeds, p_hits, p_hitoff, p_partial, p_table, p_events, p_hitlist, p_items, p_misc;
+};
+
+// Shared by both forms: batch statistics (one small device-to-host copy and
+// a stream sync) and the packed read stream.
+struct BatchPrep {
+    BatchStats st;
+    uint32_t* rwords;
+    uint64_t base0;
+};
+
+inline int grid_cap(int sms, uint64_t n, int threads) {
+    uint64_t want = (n + threads - 1) / threads;
+    const uint64_t cap = (uint64_t)sms * 16;
+    if (want > cap) want = cap;
+    if (want < 1) want = 1;
+    return (int)want;
+}
+
+int prepare_batch(const snap_index* idx, Engine* e, const uint8_t* d_reads,
+                  const uint64_t* d_offsets, uint64_t n, const snap_params* p,
+                  cudaStream_t stream, BatchPrep* out, const char* where);
+
+}  // namespace snapgpu

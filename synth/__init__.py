@@ -235,9 +235,12 @@ CONFIGS = {
                    max_dist_rule="min64_10pct"),
     # Serving loop: 3.1 Gbp, 50% repeats; 80% 100 bp, 20% log-uniform [1000,10000];
     # 5% total error, 20% of it indels (lengths 1-20); d_max = max(8, ceil(0.08 m)).
+    # "5% total error" is read as 5% of bases in error: 4% substituted bases plus indel
+    # events at 1%/10.5 per base (mean indel length 10.5), so about 1% of bases in indels.
     "C4": Workload("C4-serving-3.1Gbp", G=3_100_000_000, repeat_frac=0.50, n_reads=0,
                    len_mode=2, m_fixed=100, len_lo=1000, len_hi=10000, frac_fixed=0.8,
-                   sub_rate=0.04, indel_rate=0.01, indel_len=(1, 20), max_dist=8, max_hits=300,
+                   sub_rate=0.04, indel_rate=0.01 / 10.5, indel_len=(1, 20), max_dist=8,
+                   max_hits=300,
                    conf_diff=2, num_seeds=0, max_dist_rule="max8_8pct",
                    extra=dict(req_lo=1000, req_hi=100000, n_requests=200)),
     # Human-scale throughput: same 3.1 Gbp genome, 100M x 100 bp, 1% sub, 0.1% indels of 1-5.

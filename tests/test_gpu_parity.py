@@ -1,0 +1,243 @@
+"""Parity of the CUDA path with the oracle (bit-exact in every result field).
+
+Every call goes through the C-ABI.  Workloads are the seeded synthetic recipes of
+synth.CONFIGS (scaled where the oracle must finish in seconds) plus the hand-built
+Algorithm 1 branch cases of test_oracle_align.py and edge cases (empty batch, reads
+shorter than a seed, seed lengths 8 and 32, ragged lengths, bad bases).
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("location", "edit_distance", "strand", "cls")
+
+
+@pytest.fixture(scope="module")
+def snap():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1111_5572_gb300 as m
+    return m
+
+
+def assert_same(got, ref, what=""):
+    for f in FIELDS:
+        if not np.array_equal(got[f], ref[f]):
+            bad = np.nonzero(got[f] != ref[f])[0]
+            i = int(bad[0])
+            raise AssertionError(f"{what}: field {f} differs at {len(bad)} reads, first {i}: "
+                                 f"gpu={got[i]} oracle={ref[i]}")
+
+
+def _run_both(snap, g, rd, w, plain=False, dpr=None, **kw):
+    params = w.params()
+    params.update(kw)
+    gi = snap.Index(g, w.seed_len)
+    got = gi.align(rd.bases, rd.offsets, max_dist_per_read=dpr, plain=plain, **params)
+    ref, st = oracle.Index(g, w.seed_len).align(rd.bases, rd.offsets, max_dist_per_read=dpr,
+                                                threads=4, **params)
+    return got, ref, st
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_c1_tiny_full(snap, plain):
+    w = synth.CONFIGS["C1"]
+    g, _ = w.make_genome()
+    rd = w.make_reads(g)
+    got, ref, st = _run_both(snap, g, rd, w, plain=plain)
+    assert_same(got, ref, f"C1 plain={plain}")
+    assert st.n_single > 9000
+
+
+@pytest.mark.parametrize("plain", [False, True])
+@pytest.mark.parametrize("G,n", [(3_000_000, 20_000)])
+def test_c2_repeat_rich_scaled(snap, G, n, plain):
+    w = synth.CONFIGS["C2"].scaled(G=G, n_reads=n)
+    g, _ = w.make_genome()
+    rd = w.make_reads(g)
+    got, ref, st = _run_both(snap, g, rd, w, plain=plain)
+    assert_same(got, ref, f"C2 scaled plain={plain}")
+    assert st.n_multiple > 0  # the repeat families exercise the multiple-hit paths
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_c3_uneven_lengths_scaled(snap, plain):
+    w = synth.CONFIGS["C3"].scaled(G=4_000_000, n_reads=4000)
+    g, _ = w.make_genome()
+    rd = w.make_reads(g)
+    dpr = w.max_dist_per_read(rd.lengths())
+    got, ref, _ = _run_both(snap, g, rd, w, dpr=dpr, plain=plain)
+    assert_same(got, ref, f"C3 scaled plain={plain}")
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_c4_long_reads_scaled(snap, plain):
+    # lengths: 80% 100 bp, 20% log-uniform [1000, 10000]; d_max = max(8, ceil(0.08 m))
+    # reaches 800, which takes the shared-memory diagonal path of the edit distance
+    w = synth.CONFIGS["C4"].scaled(G=2_000_000, n_reads=300)
+    g, _ = w.make_genome()
+    rd = w.make_reads(g, n=300)
+    dpr = w.max_dist_per_read(rd.lengths())
+    assert dpr.max() > 127
+    got, ref, _ = _run_both(snap, g, rd, w, dpr=dpr, plain=plain)
+    assert_same(got, ref, f"C4 scaled plain={plain}")
+
+
+@pytest.mark.parametrize("s", [8, 12, 31, 32])
+def test_seed_length_range(snap, s):
+    w = synth.CONFIGS["C1"].scaled(G=300_000, n_reads=2000)
+    w = replace(w, seed_len=s, num_seeds=0, max_hits=50)
+    g, _ = w.make_genome()
+    rd = w.make_reads(g)
+    got, ref, _ = _run_both(snap, g, rd, w)
+    assert_same(got, ref, f"s={s}")
+
+
+def test_ragged_and_degenerate_reads(snap):
+    g, _ = synth.genome(500_000, 0.05)
+    lens = np.array([0, 1, 19, 20, 21, 39, 40, 100, 101, 257, 1000, 5, 64, 65, 1023, 1024],
+                    dtype=np.uint32)
+    lens = np.concatenate([lens, np.random.default_rng(1).integers(0, 600, 500).astype(np.uint32)])
+    rd = synth.reads(g, lens, 0.02, 0.005, (1, 8), seed=5)
+    w = synth.CONFIGS["C1"]
+    for kw in (dict(), dict(num_seeds=17), dict(num_seeds=2047), dict(max_hits=0),
+               dict(max_hits=1), dict(max_dist=0, conf_diff=1), dict(conf_diff=5)):
+        for plain in (False, True):
+            got, ref, _ = _run_both(snap, g, rd, w, plain=plain, **kw)
+            assert_same(got, ref, f"ragged {kw} plain={plain}")
+
+
+def test_hand_built_branch_cases(snap):
+    # the genomes of test_oracle_align.py, all reads in one batch
+    rng = np.random.default_rng(2)
+    g = bytearray(np.frombuffer(b"ACGT", dtype=np.uint8)[rng.integers(0, 4, 60_000)].tobytes())
+    rc = lambda a: bytes(a)[::-1].translate(bytes.maketrans(b"ACGT", b"TGCA"))
+
+    def sub(a, i):
+        a = bytearray(a)
+        a[i] = b"CGTA"[b"ACGT".index(a[i])]
+        return bytes(a)
+
+    g[9000:9100] = g[2000:2100]                       # exact repeat: early multiple
+    a = bytes(g[3000:3100])
+    g[12000:12100] = sub(sub(a, 10), 30)              # Baeza-Yates stop
+    b = bytes(g[5000:5100])
+    g[18000:18020] = b[20:40]
+    g[24000:24020] = b[20:40]                         # drain
+    g[31000:31100] = g[1000:1100]                     # popular with h_max = 1
+    r = bytes(np.frombuffer(b"ACGT", dtype=np.uint8)[rng.integers(0, 4, 100)].tobytes())
+    g[40000:40100] = sub(r, 10)
+    g[47000:47100] = sub(r, 90)                       # distance tie
+    pal = b"ACGTTGCAAG" + rc(b"ACGTTGCAAG")
+    g[52000:52020] = pal                              # palindromic seed
+    g = bytes(g)
+    p1, p2 = 32 * 700 + 5, 32 * 800 + 31
+    reads = [g[2000:2100], a, b, g[1000:1100], r, g[52000:52100],
+             g[p1:p1 + 40] + g[p1 + 41:p1 + 101], g[p2:p2 + 40] + g[p2 + 41:p2 + 101],
+             sub(sub(sub(g[7000:7100], 25), 45), 65), rc(g[100:200]), g[59_900:60_000],
+             g[10:25], bytes(np.frombuffer(b"ACGT", dtype=np.uint8)[rng.integers(0, 4, 100)])]
+    bases = np.frombuffer(b"".join(reads), dtype=np.uint8)
+    offs = np.zeros(len(reads) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum([len(x) for x in reads])
+    gi = snap.Index(np.frombuffer(g, dtype=np.uint8), 20)
+    oi = oracle.Index(np.frombuffer(g, dtype=np.uint8), 20)
+    for kw in (dict(max_dist=8, max_hits=300, conf_diff=2), dict(max_dist=2, max_hits=1,
+                                                                 conf_diff=2),
+               dict(max_dist=8, max_hits=2, conf_diff=2)):
+        for plain in (False, True):
+            got = gi.align(bases, offs, plain=plain, **kw)
+            ref, _ = oi.align(bases, offs, **kw)
+            assert_same(got, ref, f"branch cases {kw}")
+
+
+def test_empty_batch_and_bad_input(snap):
+    g, _ = synth.genome(100_000, 0.0)
+    gi = snap.Index(g, 20)
+    out = gi.align(np.zeros(0, dtype=np.uint8), np.zeros(1, dtype=np.uint64))
+    assert out.shape == (0,)
+    bad = np.frombuffer(b"ACGTACGTNNACGTACGTACGTACGT", dtype=np.uint8)
+    with pytest.raises(snap.SnapError) as e:
+        gi.align(bad, np.array([0, bad.shape[0]], dtype=np.uint64))
+    assert e.value.code == snap.SNAP_E_INVAL
+    lower = np.frombuffer(b"acgtacgtacgtacgtacgtacgt", dtype=np.uint8)
+    with pytest.raises(snap.SnapError):
+        gi.align(lower, np.array([0, lower.shape[0]], dtype=np.uint64))
+    with pytest.raises(snap.SnapError):
+        gi.align(g[:100], np.array([0, 100], dtype=np.uint64), max_hits=70000)
+    with pytest.raises(snap.SnapError):
+        gi.align(g[:100], np.array([0, 100], dtype=np.uint64), conf_diff=0)
+    with pytest.raises(snap.SnapError):
+        gi.align(g[:100], np.array([50, 10], dtype=np.uint64))
+    # the index still works after the failed calls
+    got = gi.align(g[:100], np.array([0, 100], dtype=np.uint64))
+    assert int(got["cls"][0]) == snap.SINGLE_HIT and int(got["location"][0]) == 0
+    with pytest.raises(snap.SnapError):
+        snap.Index(np.frombuffer(b"ACGTN" * 10, dtype=np.uint8), 20)
+
+
+def test_index_info(snap):
+    w = synth.CONFIGS["C2"].scaled(G=2_000_000, n_reads=10)
+    g, _ = w.make_genome()
+    gi = snap.Index(g, 20)
+    inf = gi.info()
+    npos = 2_000_000 - 19
+    assert inf["genome_len"] == 2_000_000 and inf["seed_len"] == 20
+    assert inf["table_slots"] >= npos * 3 // 2
+    # every window's canonical s-mer is in the table; repeats share slots
+    assert 0.9 * npos < inf["distinct_seeds"] <= npos
+    # out-of-line entries = windows whose key occurs 2..65534 times
+    oi = oracle.Index(g, 20)
+    assert inf["list_entries"] <= npos
+
+
+def test_device_entry_point_on_torch_stream(snap):
+    import torch
+    w = synth.CONFIGS["C1"].scaled(G=500_000, n_reads=5000)
+    g, _ = w.make_genome()
+    rd = w.make_reads(g)
+    gi = snap.Index(g, 20)
+    dev = torch.device("cuda:0")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        d_b = torch.from_numpy(rd.bases).to(dev, non_blocking=False)
+        d_o = torch.from_numpy(rd.offsets.view(np.int64)).to(dev)
+        d_out = torch.zeros((rd.n, 16), dtype=torch.uint8, device=dev)
+    s.synchronize()
+    gi.align_device(d_b, d_o, d_out, stream=s, **w.params())
+    got = d_out.cpu().numpy().view(snap.RESULT_DTYPE).reshape(-1)
+    ref, _ = oracle.Index(g, 20).align(rd.bases, rd.offsets, **w.params())
+    assert_same(got, ref, "device entry point")
+    # unaligned read start: offsets into the middle of the buffer
+    sub = np.arange(1, rd.n)
+    offs2 = rd.offsets[1:].copy()
+    got2 = gi.align(rd.bases, offs2, **w.params())
+    assert_same(got2, ref[1:], "offset base not 16-aligned")
+
+
+def test_c2_full_size_sampled(snap):
+    """The benchmark workload (100 Mbp, 5% repeats, 1M x 100 bp) in the launch the bench
+    times; the oracle checks a sample of 20,000 reads with an index restricted to the
+    seeds those reads look up."""
+    w = synth.CONFIGS["C2"]
+    g, _ = w.make_genome()
+    rd = w.make_reads(g)
+    gi = snap.Index(g, w.seed_len)
+    got = gi.align(rd.bases, rd.offsets, **w.params())
+    sample = np.sort(np.random.default_rng(42).choice(rd.n, 20_000, replace=False))
+    sub = rd.subset(sample)
+    keys = oracle.read_seed_kmers(sub.bases, sub.offsets, w.seed_len, w.num_seeds)
+    oi = oracle.Index(g, w.seed_len, kmer_filter=keys)
+    ref, st = oi.align(sub.bases, sub.offsets, threads=8, **w.params())
+    assert_same(got[sample], ref, "C2 full-size sample")
+    # properties that hold for every read: classes valid, located hits within d_max
+    assert set(np.unique(got["cls"]).tolist()) <= {0, 1, 2}
+    loc = got["location"] >= 0
+    assert (got["edit_distance"][loc] <= w.max_dist).all()
+    assert (got["location"][loc] < w.G).all()
+    assert ((got["location"] == -1) == (got["edit_distance"] == -1)).all()
