@@ -53,8 +53,14 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--profile", action="store_true",
+                    help="warm-up plus the timed steps only (no plain form, e2e or CPU "
+                         "baseline): the command to run under ncu")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.profile:
+        args.no_plain = args.no_cpu_baseline = True
+        args.e2e_steps = 0
     return args
 
 
@@ -350,7 +356,7 @@ def run_ours(args):
             line["plain"] = {"error": str(e)[:200]}
 
     # e2e through the public host-buffer call: pinned inputs in, results out
-    if rank == 0 or ws > 1:
+    if args.e2e_steps > 0:
         pin_b = torch.from_numpy(rd.bases).pin_memory()
         pin_o = torch.from_numpy(rd.offsets.view(np.int64)).pin_memory()
         pin_out = torch.zeros((n, 16), dtype=torch.uint8).pin_memory()

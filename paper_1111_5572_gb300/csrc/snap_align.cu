@@ -68,11 +68,23 @@ __global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, i
         my_n = max(my_n, nn);
         my_hits = max(my_hits, (unsigned long long)nn * (unsigned long long)h_max);
     }
-    if (bad) atomicOr(&st->status, bad);
-    atomicMax(&st->max_len, my_len);
-    atomicMax(&st->max_L0, my_L0);
-    atomicMax(&st->max_seeds, my_n);
-    atomicMax(&st->max_hits_bound, my_hits);
+    // one atomic per warp and field (all threads of a warp reach this point)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bad |= __shfl_xor_sync(kFull, bad, o);
+        my_len = max(my_len, __shfl_xor_sync(kFull, my_len, o));
+        my_L0 = max(my_L0, __shfl_xor_sync(kFull, my_L0, o));
+        my_n = max(my_n, __shfl_xor_sync(kFull, my_n, o));
+        const unsigned long long h = __shfl_xor_sync(kFull, my_hits, o);
+        my_hits = h > my_hits ? h : my_hits;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicOr(&st->status, bad);
+        atomicMax(&st->max_len, my_len);
+        atomicMax(&st->max_L0, my_L0);
+        atomicMax(&st->max_seeds, my_n);
+        atomicMax(&st->max_hits_bound, my_hits);
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->total_bases = offsets[n] - offsets[0];
         if (offsets[n] < offsets[0]) atomicOr(&st->status, kStBadOffsets);
@@ -217,10 +229,13 @@ struct WarpMem {
     HitRec* ghits;
 };
 
-// Edit distance of candidate `key` at limit L (warp-wide, result uniform).
+// Edit distance of candidate `key` at limit L (warp-wide, result uniform).  LVD
+// selects the diagonal layout: D diagonals per lane in registers (L <= 32D/2 - 1)
+// or 0 for shared memory (any L).  One variant per kernel keeps the code small.
+template <int LVD>
 __device__ __forceinline__ int candidate_distance(const FusedArgs& a, const WarpMem& wm, int m,
-                                                  unsigned long long key, int L, int lane,
-                                                  WarpCounters& wc) {
+                                               unsigned long long key, int L, int lane,
+                                               WarpCounters& wc) {
     if (L < 0) return kOver;
     const uint64_t p = key >> 1;
     const int strand = (int)(key & 1);
@@ -231,8 +246,13 @@ __device__ __forceinline__ int candidate_distance(const FusedArgs& a, const Warp
     const int nwt = (tb + n_t + 15) / 16 + 2;
     for (int w = lane; w < nwt; w += 32) wm.Tw[w] = __ldg(a.genome + w0 + w);
     __syncwarp();
-    const int d = lv_warp(strand ? wm.Xr : wm.Xf, m, wm.Tw, tb, n_t, L, lane, wm.lvA, wm.lvB,
-                          a.status);
+    int d;
+    if constexpr (LVD > 0) {
+        d = lv_warp_reg<LVD>(strand ? wm.Xr : wm.Xf, m, wm.Tw, tb, n_t, L, lane);
+    } else {
+        d = lv_warp(strand ? wm.Xr : wm.Xf, m, wm.Tw, tb, n_t, L, lane, wm.lvA, wm.lvB,
+                    a.status);
+    }
     __syncwarp();
     if (lane == 0) {
         wc.window_words += (unsigned)nwt;
@@ -242,8 +262,9 @@ __device__ __forceinline__ int candidate_distance(const FusedArgs& a, const Warp
     return d;
 }
 
-__device__ void align_one_read(const FusedArgs& a, const WarpMem& wm, uint64_t r, int lane,
-                               WarpCounters& wc) {
+template <int LVD>
+__device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem& wm, uint64_t r,
+                                               int lane, WarpCounters& wc) {
     const uint64_t o0 = a.offsets[r], o1 = a.offsets[r + 1];
     const int m = (int)(o1 - o0);
     const uint64_t rb = o0 - a.base0 + kReadPadBases;
@@ -335,7 +356,7 @@ __device__ void align_one_read(const FusedArgs& a, const WarpMem& wm, uint64_t r
                 const uint32_t slot = (uint32_t)(packed & 0xfffffu);
                 const unsigned long long key = kKeyMask - ((packed >> 20) & kKeyMask);
                 const int L = limit();
-                const int d = candidate_distance(a, wm, m, key, L, lane, wc);
+                const int d = candidate_distance<LVD>(a, wm, m, key, L, lane, wc);
                 if (lane == 0) {
                     tab[slot].state = d >= 0 ? d : kOver;
                     if (d >= 0) {
@@ -365,10 +386,18 @@ __device__ void align_one_read(const FusedArgs& a, const WarpMem& wm, uint64_t r
                 }
             };
 
-            for (int i = 0; i < n; ++i) {
-                const SeedRec rec = wm.seeds[i];
-                if (rec.flags & kSeedPopular) continue;
-                any_nonpopular = true;
+            // One pass per non-popular seed: add its votes, pick and score one
+            // candidate, test the exits.  Once the Baeza-Yates test passes the loop
+            // only picks and scores (no early return) until nothing is left.
+            bool draining = false;
+            int i = 0;
+            for (;;) {
+                SeedRec rec;
+                if (!draining) {
+                    while (i < n && (wm.seeds[i].flags & kSeedPopular)) ++i;
+                    if (i >= n) break;
+                    rec = wm.seeds[i++];
+                    any_nonpopular = true;
                 const int o = rec.offset;
                 const int tot = (int)rec.fwd_n + rec.rc_n;
                 for (int j = lane; j < tot; j += 32) {
@@ -390,19 +419,19 @@ __device__ void align_one_read(const FusedArgs& a, const WarpMem& wm, uint64_t r
                 }
                 __syncwarp();
                 if (rec.flags & kSeedPass0) ++t;
+                }
                 const unsigned long long pk = table_pick(tab, cap, lane);
-                if (pk) score(pk);
-                if (d_best < c && d_second < d_best + c) {
-                    returned = true;
+                if (pk) {
+                    score(pk);
+                } else if (draining) {
                     break;
                 }
-                if (t >= d_best + c) {
-                    for (;;) {
-                        const unsigned long long q = table_pick(tab, cap, lane);
-                        if (!q) break;
-                        score(q);
+                if (!draining) {
+                    if (d_best < c && d_second < d_best + c) {
+                        returned = true;
+                        break;
                     }
-                    break;
+                    if (t >= d_best + c) draining = true;
                 }
             }
             const bool all_popular = !any_nonpopular;  // n >= 1 here
@@ -430,7 +459,8 @@ __device__ void align_one_read(const FusedArgs& a, const WarpMem& wm, uint64_t r
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(256) k_align_fused(FusedArgs a) {
+template <int LVD>
+__global__ void __launch_bounds__(256, 4) k_align_fused(FusedArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t* base = smem + (size_t)wib * a.warp_words;
@@ -453,9 +483,21 @@ __global__ void __launch_bounds__(256) k_align_fused(FusedArgs a) {
         it = __shfl_sync(kFull, it, 0);
         if (it >= a.n_items) break;
         const uint64_t r = a.order ? a.order[it] : it;
-        align_one_read(a, wm, r, lane, wc);
+        align_one_read<LVD>(a, wm, r, lane, wc);
     }
     flush_counters(a.ctr, wc);
+}
+
+using FusedKernel = void (*)(FusedArgs);
+
+// The kernel variant for a batch whose largest limit is Lmax: the fewest
+// register diagonals per lane that cover [-Lmax, Lmax], else shared memory.
+static FusedKernel fused_kernel_for(int Lmax) {
+    if (Lmax <= 15) return k_align_fused<1>;
+    if (Lmax <= 31) return k_align_fused<2>;
+    if (Lmax <= 63) return k_align_fused<4>;
+    if (Lmax <= 127) return k_align_fused<8>;
+    return k_align_fused<0>;
 }
 
 // ---------------------------------------------------------------------------
@@ -722,12 +764,14 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
     a.wt = up4((mmax + Lmax + 15 + 15) / 16 + 4);
     a.seed_cap = nmax;
     a.lv_ints = Lmax > 127 ? up4(2 * (2 * Lmax + 4)) : 0;
-    // shared table: as large as the per-block budget allows, 64..1024 slots
+    // shared table: 128 slots holds the candidates of a read with up to 64 seed
+    // hits (almost every short read); reads with more use the warp's global table.
+    // A small per-warp footprint keeps many warps resident per SM.
     const int fixed_words = 2 * a.wx + a.wt + 4 * a.seed_cap + a.lv_ints;
     int warps = 8;
     const int budget_words = 200 * 1024 / 4;  // per block
     while (warps > 1 && warps * (fixed_words + 6 * 64) > budget_words) warps >>= 1;
-    int scap = 1024;
+    int scap = 128;
     while (scap > 64 && warps * (fixed_words + 6 * scap) > budget_words) scap >>= 1;
     a.scap = scap;
     a.off_xr = a.wx;
@@ -747,12 +791,11 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
                   (size_t)a.warp_words * 4);
         return SNAP_E_INVAL;
     }
-    SNAP_CUDA(cudaFuncSetAttribute(k_align_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem),
+    const FusedKernel kfn = fused_kernel_for(Lmax);
+    SNAP_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
               "smem attr");
     int per_sm = 0;
-    SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_align_fused, warps * 32,
-                                                            smem),
+    SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem),
               "occupancy");
     if (per_sm < 1) per_sm = 1;
     uint64_t blocks = (uint64_t)e->sms * per_sm;
@@ -783,7 +826,7 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
     a.head = static_cast<unsigned long long*>(e->head.p);
     SNAP_CUDA(cudaMemsetAsync(a.head, 0, sizeof(unsigned long long), stream), "head clear");
     e->launches++;
-    k_align_fused<<<(unsigned)blocks, warps * 32, smem, stream>>>(a);
+    kfn<<<(unsigned)blocks, warps * 32, smem, stream>>>(a);
     SNAP_CUDA(cudaGetLastError(), "align launch");
     return SNAP_OK;
 }

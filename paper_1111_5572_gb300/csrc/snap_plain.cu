@@ -295,7 +295,9 @@ __global__ void k_plain_replay(PlainArgs a) {
                 unsigned long long best = 0;
                 for (uint32_t j = lane; j < cap; j += 32) {
                     const CandSlot e = tab[j];
-                    if (e.key != kEmptyKey && !(e.votes & kScoredBit)) {
+                    // the table holds every seed's keys from the start; a key takes part
+                    // only once a seed processed so far has voted for it
+                    if (e.key != kEmptyKey && e.votes != 0 && !(e.votes & kScoredBit)) {
                         const unsigned long long v = ((unsigned long long)e.votes << 53) |
                                                      ((kKeyMaskP - e.key) << 20) | j;
                         best = v > best ? v : best;
