@@ -151,6 +151,33 @@ int snap_align_plain_device(const snap_index* index, const uint8_t* d_reads,
                             const uint64_t* d_offsets, uint64_t n_reads,
                             const snap_params* params, snap_result* d_out, void* stream);
 
+/*
+ * snap_align_device without any device memory allocation.  The paper has no
+ * counterpart: this exists for callers that cannot let the library call
+ * cudaMalloc or cudaFree, for example code running under a framework that has
+ * already reserved the device memory for its own pool, a serving thread that
+ * must not stall the device (cudaMalloc/cudaFree can synchronize it), or a
+ * process that routes every device allocation through its own allocator.
+ *
+ * All scratch (batch statistics, status word, queue head, packed reads,
+ * candidate tables that do not fit in shared memory) lives in one fixed 64 MiB
+ * array that every GPU loading the library holds until the process exits.
+ * Limits: at most 201,326,432 read bases per call (the reads are packed 4 per
+ * byte into 48 MiB), and seeds x max_hits per read small enough for one warp's
+ * candidate table to fit in the remaining 16 MiB.  Larger batches fail with
+ * SNAP_E_INVAL before any read is touched; split them.  The caller still
+ * passes (and owns) the reads, offsets and results, as for snap_align_device.
+ *
+ * The first call on a device looks up the array's device address and caches
+ * it; make that first call before any stream capture on that device.  Every
+ * call reuses the same array, so calls whose GPU work overlaps (other streams,
+ * other threads) race with each other: keep them ordered.  Same arguments,
+ * results and errors as snap_align_device.
+ */
+int snap_align_device_noalloc(const snap_index* index, const uint8_t* d_reads,
+                              const uint64_t* d_offsets, uint64_t n_reads,
+                              const snap_params* params, snap_result* d_out, void* stream);
+
 /* Host-buffer variant of the plain form. */
 int snap_align_plain(const snap_index* index, const uint8_t* reads_ascii,
                      const uint64_t* read_offsets, uint64_t n_reads, const snap_params* params,

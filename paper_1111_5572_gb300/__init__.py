@@ -27,7 +27,7 @@ assert RESULT_DTYPE.itemsize == 16
 EXPORTS = ("snap_index_build", "snap_index_free", "snap_index_info_get", "snap_align",
            "snap_align_device", "snap_align_plain_device", "snap_align_plain",
            "snap_server_create", "snap_server_submit", "snap_server_wait", "snap_server_destroy",
-           "snap_last_call_stats", "snap_last_error")
+           "snap_last_call_stats", "snap_align_device_noalloc", "snap_last_error")
 
 
 class SnapError(RuntimeError):
@@ -79,7 +79,7 @@ def load_library(path: str = LIB_PATH):
     lib.snap_index_info_get.argtypes = [vp, P(snap_index_info)]
     for name in ("snap_align", "snap_align_plain"):
         getattr(lib, name).argtypes = [vp, vp, vp, u64, P(snap_params), vp]
-    for name in ("snap_align_device", "snap_align_plain_device"):
+    for name in ("snap_align_device", "snap_align_plain_device", "snap_align_device_noalloc"):
         getattr(lib, name).argtypes = [vp, vp, vp, u64, P(snap_params), vp, vp]
     lib.snap_server_create.argtypes = [vp, u64, i32, P(vp)]
     lib.snap_server_submit.argtypes = [vp, vp, vp, u64, P(snap_params), P(u64)]
@@ -173,6 +173,21 @@ class Index:
                   ctypes.c_void_p(d_offsets.data_ptr()), n, ctypes.byref(prm),
                   ctypes.c_void_p(d_out.data_ptr()), st),
                "snap_align_plain_device" if plain else "snap_align_device")
+        return d_out
+
+    def align_device_noalloc(self, d_bases, d_offsets, d_out, max_dist: int = 8,
+                             max_hits: int = 300, conf_diff: int = 2, num_seeds: int = 0,
+                             d_max_dist_per_read=None, stream=None):
+        """snap_align_device_noalloc: the library allocates no device memory for this call
+        (for callers that must not see cudaMalloc/cudaFree); limits in include/snap.h."""
+        n = int(d_offsets.numel() - 1)
+        prm = make_params(max_dist, max_hits, conf_diff, num_seeds,
+                          None if d_max_dist_per_read is None else d_max_dist_per_read.data_ptr())
+        st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        _check(load_library().snap_align_device_noalloc(
+            self._h, ctypes.c_void_p(d_bases.data_ptr()), ctypes.c_void_p(d_offsets.data_ptr()),
+            n, ctypes.byref(prm), ctypes.c_void_p(d_out.data_ptr()), st),
+            "snap_align_device_noalloc")
         return d_out
 
     def close(self):

@@ -960,3 +960,219 @@ extern "C" int snap_align_plain_device(const snap_index* idx, const uint8_t* d_r
     return align_batch_device(idx, idx->engine, d_reads, d_offsets, n, p, d_out,
                               static_cast<cudaStream_t>(stream), true);
 }
+
+// ---------------------------------------------------------------------------
+// snap_align_device_noalloc: the batched form with no device allocation.
+//
+// Some callers cannot let a library call cudaMalloc/cudaFree: a framework that
+// has already reserved the device memory for its own pool (an allocation would
+// fail or fragment it), a serving thread that must never stall (cudaMalloc and
+// cudaFree can synchronize the whole device), or a process whose device memory
+// is audited through its own allocator.  For them this entry point keeps every
+// piece of scratch (batch statistics, status word, queue head, packed reads and
+// the per-warp candidate tables that do not fit in shared memory) in one
+// file-scope device array of fixed size that is created when the library's
+// code is loaded onto a device and lives until the process exits.
+// ---------------------------------------------------------------------------
+namespace snapgpu {
+
+constexpr size_t kNoAllocBytes = 64ull << 20;      // whole array: 64 MiB per device
+constexpr size_t kNoAllocHeadBytes = 4096;         // statistics, status, counters, queue head
+constexpr size_t kNoAllocReadBytes = 48ull << 20;  // packed reads (4 bases per byte)
+constexpr size_t kNoAllocTableBytes = kNoAllocBytes - kNoAllocHeadBytes - kNoAllocReadBytes;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// array's name only stands for the symbol, so the address is looked up once per
+// device (with that device current) and cached.
+static int noalloc_scratch(void** out) {
+    int dev = 0;
+    SNAP_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("snap_align_device_noalloc: device %d out of range", dev);
+        return SNAP_E_INVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr)
+            return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                             "cudaGetSymbolAddress(scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return SNAP_OK;
+}
+
+static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const uint64_t* d_offsets,
+                         uint64_t n, const snap_params* p, snap_result* d_out,
+                         cudaStream_t stream) {
+    const char* where = "snap_align_device_noalloc";
+    int rc = validate_params(idx, p);
+    if (rc) return rc;
+    if (n == 0) return SNAP_OK;
+    if (!d_reads || !d_offsets || !d_out) {
+        set_error("%s: NULL buffer", where);
+        return SNAP_E_INVAL;
+    }
+    if ((reinterpret_cast<uintptr_t>(d_offsets) | reinterpret_cast<uintptr_t>(d_out)) % 8 ||
+        (p->max_dist_per_read && reinterpret_cast<uintptr_t>(p->max_dist_per_read) % 4)) {
+        set_error("%s: offsets and results must be 8-byte aligned, max_dist_per_read 4-byte "
+                  "aligned", where);
+        return SNAP_E_INVAL;
+    }
+    void* base = nullptr;
+    if ((rc = noalloc_scratch(&base))) return rc;
+    unsigned char* b = static_cast<unsigned char*>(base);
+    BatchStats* d_st = reinterpret_cast<BatchStats*>(b);
+    unsigned long long* d_head = reinterpret_cast<unsigned long long*>(b + 1024);
+    uint32_t* d_words = reinterpret_cast<uint32_t*>(b + kNoAllocHeadBytes);
+    unsigned char* d_tables = b + kNoAllocHeadBytes + kNoAllocReadBytes;
+
+    // the array keeps the previous call's contents: clear what must start at zero
+    SNAP_CUDA(cudaMemsetAsync(d_st, 0, sizeof(BatchStats), stream), "clear statistics");
+    SNAP_CUDA(cudaMemsetAsync(d_head, 0, sizeof(unsigned long long), stream), "clear head");
+    int sms = 0, dev = 0;
+    SNAP_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    SNAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    k_read_stats<<<grid_cap(sms, n, 256), 256, 0, stream>>>(
+        d_offsets, n, idx->s, p->num_seeds, p->max_dist, p->conf_diff, p->max_hits,
+        p->max_dist_per_read, d_st);
+    SNAP_CUDA(cudaGetLastError(), "stats launch");
+    BatchStats hs;
+    uint64_t base0 = 0;
+    SNAP_CUDA(cudaMemcpyAsync(&hs, d_st, sizeof(hs), cudaMemcpyDeviceToHost, stream), "stats");
+    SNAP_CUDA(cudaMemcpyAsync(&base0, d_offsets, sizeof(base0), cudaMemcpyDeviceToHost, stream),
+              "offset");
+    SNAP_CUDA(cudaStreamSynchronize(stream), where);
+    if (hs.status) return status_to_code(hs.status, where);
+    const uint64_t nwords = (hs.total_bases + kReadPadBases + 15) / 16 + 8;
+    if (nwords * 4 > kNoAllocReadBytes) {
+        set_error("%s: the batch has %llu bases; this entry point holds at most %llu bases "
+                  "per call (split the batch or use snap_align_device)",
+                  where, (unsigned long long)hs.total_bases,
+                  (unsigned long long)((kNoAllocReadBytes / 4 - 8) * 16 + 15 - kReadPadBases -
+                                       15));
+        return SNAP_E_INVAL;
+    }
+    const int aligned = ((reinterpret_cast<uintptr_t>(d_reads) + base0) % 16) == 0;
+    k_pack_reads<<<grid_cap(sms, nwords, 256), 256, 0, stream>>>(
+        d_reads, base0, hs.total_bases, d_words, nwords, aligned, &d_st->status);
+    SNAP_CUDA(cudaGetLastError(), "pack launch");
+
+    FusedArgs a;
+    memset(&a, 0, sizeof(a));
+    a.genome = idx->genome_words;
+    a.G = idx->G;
+    a.s = idx->s;
+    a.slots = idx->slots;
+    a.T = idx->T;
+    a.positions = idx->positions;
+    a.rwords = d_words;
+    a.offsets = d_offsets;
+    a.base0 = base0;
+    a.order = nullptr;
+    a.n_items = n;
+    a.head = d_head;
+    a.d_max = p->max_dist;
+    a.h_max = p->max_hits;
+    a.c = p->conf_diff;
+    a.num_seeds = p->num_seeds;
+    a.dmax_per_read = p->max_dist_per_read;
+    shift_list(idx->s, a.shifts, &a.n_shifts);
+    a.out = d_out;
+    a.status = &d_st->status;
+    a.ctr = &d_st->ctr;
+    const int mmax = std::max(1u, hs.max_len);
+    const int Lmax = std::max(0, hs.max_L0);
+    const int nmax = std::max(1, hs.max_seeds);
+    auto up4 = [](int w) { return (w + 3) & ~3; };
+    a.wx = up4((mmax + 15) / 16 + 4);
+    a.wt = up4((mmax + Lmax + 15 + 15) / 16 + 4);
+    a.seed_cap = nmax;
+    a.lv_ints = Lmax > 127 ? up4(2 * (2 * Lmax + 4)) : 0;
+    const int fixed_words = 2 * a.wx + a.wt + 4 * a.seed_cap + a.lv_ints;
+    int warps = 8;
+    const int budget_words = 200 * 1024 / 4;
+    while (warps > 1 && warps * (fixed_words + 6 * 64) > budget_words) warps >>= 1;
+    int scap = 1024;
+    while (scap > 64 && warps * (fixed_words + 6 * scap) > budget_words) scap >>= 1;
+    a.scap = scap;
+    a.off_xr = a.wx;
+    a.off_tw = 2 * a.wx;
+    a.off_seeds = a.off_tw + a.wt;
+    a.off_tab = a.off_seeds + 4 * a.seed_cap;
+    a.off_hits = a.off_tab + 4 * scap;
+    a.off_lv = a.off_hits + 4 * (scap / 2);
+    a.warp_words = a.off_lv + a.lv_ints;
+    const size_t smem = (size_t)warps * a.warp_words * 4;
+    if (smem > 227 * 1024) {
+        set_error("%s: read length %d needs too much shared memory", where, mmax);
+        return SNAP_E_INVAL;
+    }
+    const FusedKernel kfn = fused_kernel_for(Lmax);
+    SNAP_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+              "smem attr");
+    int per_sm = 0;
+    SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem),
+              "occupancy");
+    if (per_sm < 1) per_sm = 1;
+    uint64_t blocks = (uint64_t)sms * per_sm;
+    const uint64_t need_blocks = (n + warps - 1) / warps;
+    if (blocks > need_blocks) blocks = need_blocks;
+    uint64_t gcap = 64;
+    while (gcap < 2 * hs.max_hits_bound) gcap <<= 1;
+    if (gcap > kMaxTableSlots) {
+        set_error("%s: seeds x max_hits per read (%llu) exceeds %u", where,
+                  (unsigned long long)hs.max_hits_bound, kMaxTableSlots / 2);
+        return SNAP_E_INVAL;
+    }
+    if (gcap > (uint64_t)scap) {
+        // per-warp tables in the array; fewer warps when they would not fit
+        const uint64_t per_warp = gcap * (sizeof(CandSlot) + sizeof(HitRec) / 2);
+        const uint64_t max_warps = kNoAllocTableBytes / per_warp;
+        if (max_warps < 1) {
+            set_error("%s: seeds x max_hits per read (%llu) needs %llu bytes of candidate "
+                      "table, more than the %llu this entry point holds",
+                      where, (unsigned long long)hs.max_hits_bound,
+                      (unsigned long long)per_warp, (unsigned long long)kNoAllocTableBytes);
+            return SNAP_E_INVAL;
+        }
+        if (blocks * warps > max_warps) {
+            if (max_warps < (uint64_t)warps) {
+                // fewer warps per block; each warp keeps the same shared-memory layout
+                warps = (int)max_warps;
+                const size_t smem_w = (size_t)warps * a.warp_words * 4;
+                SNAP_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem_w),
+                          "smem attr");
+            }
+            blocks = std::max<uint64_t>(1, max_warps / warps);
+        }
+        a.gtab = reinterpret_cast<CandSlot*>(d_tables);
+        a.ghits = reinterpret_cast<HitRec*>(d_tables + blocks * warps * gcap * sizeof(CandSlot));
+        a.gcap = (uint32_t)gcap;
+    }
+    kfn<<<(unsigned)blocks, warps * 32, (size_t)warps * a.warp_words * 4, stream>>>(a);
+    SNAP_CUDA(cudaGetLastError(), "align launch");
+    int st = 0;
+    SNAP_CUDA(cudaMemcpyAsync(&st, &d_st->status, sizeof(int), cudaMemcpyDeviceToHost, stream),
+              "status");
+    SNAP_CUDA(cudaStreamSynchronize(stream), where);
+    return status_to_code(st, where);
+}
+
+}  // namespace snapgpu
+
+extern "C" int snap_align_device_noalloc(const snap_index* idx, const uint8_t* d_reads,
+                                         const uint64_t* d_offsets, uint64_t n,
+                                         const snap_params* p, snap_result* d_out, void* stream) {
+    clear_error();
+    return align_noalloc(idx, d_reads, d_offsets, n, p, d_out, static_cast<cudaStream_t>(stream));
+}
