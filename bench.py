@@ -311,7 +311,7 @@ def run_ours(args):
     st = stats[-1]
     align_ms = float(np.mean([s["align_ms"] for s in stats]))
     alg_bytes = (st["read_bases"] / 4 + 8 * st["reads"] + 16 * st["reads"] +
-                 32 * st["slot_reads"] + 4 * st["list_entries"] + st["window_bytes"])
+                 16 * st["slot_reads"] + 4 * st["list_entries"] + st["window_bytes"])
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (align_ms / 1e3) / 1e9
     kname = "k_align_plain_stages" if plain else "k_align_fused"

@@ -91,7 +91,7 @@ typedef struct {
     uint64_t genome_len;
     int32_t seed_len;
     int32_t reserved;
-    uint64_t table_slots;     /* open-addressing slots (16 bytes each) */
+    uint64_t table_slots;     /* open-addressing slots (16 bytes each, 4 per bucket) */
     uint64_t distinct_seeds;  /* occupied slots: distinct canonical s-mers */
     uint64_t list_entries;    /* positions stored out of line (keys seen 2..65534 times) */
     uint64_t device_bytes;    /* device memory held by the index */
@@ -210,8 +210,9 @@ int snap_server_destroy(snap_server* server);
  * Measurements of the last successful align call on an index (any form):
  * device time per stage from CUDA events recorded on the call's stream, the
  * number of library kernels it launched, and traffic counters kept by the
- * kernels (each index probe step reads one 16-byte slot; out-of-line list
- * entries are 4 bytes; a scored candidate stages its genome window).
+ * kernels (index probes read 64-byte buckets of four 16-byte slots and
+ * slot_reads counts the slots read; out-of-line list entries are 4 bytes; a
+ * scored candidate stages its genome window).
  */
 typedef struct {
     uint64_t kernel_launches;

@@ -42,7 +42,7 @@ __global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, i
                              const int32_t* __restrict__ dmax_per_read, BatchStats* st) {
     unsigned int my_len = 0;
     int my_L0 = 0, my_n = 0, bad = 0;
-    unsigned long long my_hits = 0;
+    unsigned long long my_hits = 0, my_light = 0;
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
          r += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t a = offsets[r], b = offsets[r + 1];
@@ -65,6 +65,8 @@ __global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, i
         if (dm < 0) bad |= kStBadDmax;
         my_len = max(my_len, (unsigned int)m);
         my_L0 = max(my_L0, dm + c - 1);
+        my_light += (m <= (uint64_t)kLightBucketMaxM && nn <= kLightBucketMaxSeeds &&
+                     dm + c - 1 <= kLightBucketMaxL);
         my_n = max(my_n, nn);
         my_hits = max(my_hits, (unsigned long long)nn * (unsigned long long)h_max);
     }
@@ -77,6 +79,7 @@ __global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, i
         my_n = max(my_n, __shfl_xor_sync(kFull, my_n, o));
         const unsigned long long h = __shfl_xor_sync(kFull, my_hits, o);
         my_hits = h > my_hits ? h : my_hits;
+        my_light += __shfl_xor_sync(kFull, my_light, o);
     }
     if ((threadIdx.x & 31) == 0) {
         if (bad) atomicOr(&st->status, bad);
@@ -84,6 +87,7 @@ __global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, i
         atomicMax(&st->max_L0, my_L0);
         atomicMax(&st->max_seeds, my_n);
         atomicMax(&st->max_hits_bound, my_hits);
+        if (my_light) atomicAdd(&st->n_light, my_light);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->total_bases = offsets[n] - offsets[0];
@@ -177,6 +181,7 @@ struct FusedArgs {
     uint64_t base0;
     const uint32_t* order;  // processing order of read ids (NULL = identity)
     uint64_t n_items;
+    const unsigned long long* n_items_dev;  // when set, the item count is read from here
     unsigned long long* head;
     int d_max, h_max, c, num_seeds;
     const int32_t* dmax_per_read;
@@ -477,11 +482,12 @@ __global__ void __launch_bounds__(256, 4) k_align_fused(FusedArgs a) {
     wm.gtab = a.gtab ? a.gtab + gw * a.gcap : nullptr;
     wm.ghits = a.ghits ? a.ghits + gw * (a.gcap / 2) : nullptr;
     WarpCounters wc;
+    const unsigned long long n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
     for (;;) {
         unsigned long long it = 0;
         if (lane == 0) it = atomicAdd(a.head, 1ull);
         it = __shfl_sync(kFull, it, 0);
-        if (it >= a.n_items) break;
+        if (it >= n_items) break;
         const uint64_t r = a.order ? a.order[it] : it;
         align_one_read<LVD>(a, wm, r, lane, wc);
     }
@@ -825,6 +831,20 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
     if ((rc = e->head.ensure(64, "queue head"))) return rc;
     a.head = static_cast<unsigned long long*>(e->head.p);
     SNAP_CUDA(cudaMemsetAsync(a.head, 0, sizeof(unsigned long long), stream), "head clear");
+    if (bp.st.n_light > 0) {
+        // short reads: one thread each; the warp kernel then takes the rest
+        if ((rc = e->heavy.ensure(n * sizeof(uint32_t), "read list"))) return rc;
+        unsigned long long* heavy_count = a.head + 1;
+        uint32_t* heavy_ids = static_cast<uint32_t*>(e->heavy.p);
+        if ((rc = launch_light(idx, e, d_offsets, n, p, d_out, stream, bp, heavy_ids,
+                               heavy_count)))
+            return rc;
+        a.order = heavy_ids;
+        a.n_items_dev = heavy_count;
+        blocks = (uint64_t)e->sms * per_sm;
+        if (a.gtab && blocks * warps * gcap * sizeof(CandSlot) > e->gtab.bytes)
+            blocks = e->gtab.bytes / (warps * gcap * sizeof(CandSlot));
+    }
     e->launches++;
     kfn<<<(unsigned)blocks, warps * 32, smem, stream>>>(a);
     SNAP_CUDA(cudaGetLastError(), "align launch");

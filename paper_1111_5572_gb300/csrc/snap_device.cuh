@@ -64,10 +64,6 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t k) {
     k ^= k >> 33;
     return k;
 }
-__device__ __forceinline__ uint64_t home_slot(uint64_t key, uint64_t T) {
-    return __umul64hi(mix64(key), T);
-}
-
 __device__ __forceinline__ IndexSlot load_slot(const IndexSlot* slots, uint64_t i) {
     const uint4 v = __ldg(reinterpret_cast<const uint4*>(slots) + i);
     IndexSlot s;
@@ -78,21 +74,44 @@ __device__ __forceinline__ IndexSlot load_slot(const IndexSlot* slots, uint64_t 
     return s;
 }
 
-// Probe the open-addressing table for canonical key K.  Returns true and the
-// slot when present.  Sets kStProbeRunaway in *status if the probe sequence
-// does not end within T slots (a full table; cannot happen at load <= 2/3).
+// The index table is a sequence of 64-byte buckets of four slots (T is a
+// multiple of 4).  A key lives in its home bucket mulhi(mix(key), T/4) or, when
+// that bucket was full at insertion, in the next non-full bucket; slots of a
+// bucket fill in order, so an empty slot ends a lookup.
+constexpr int kBucketSlots = 4;
+
+__device__ __forceinline__ uint64_t home_bucket(uint64_t key, uint64_t T) {
+    return __umul64hi(mix64(key), T / kBucketSlots);
+}
+
+// Probe for canonical key K.  Returns true and the slot when present.  Sets
+// kStProbeRunaway in *status if the probe does not end within the table (a full
+// table; cannot happen at load <= 2/3).  *steps counts slots read.
 __device__ __forceinline__ bool probe_index(const IndexSlot* slots, uint64_t T, uint64_t K,
                                             IndexSlot* out, int* status, uint32_t* steps) {
-    uint64_t i = home_slot(K, T);
-    for (uint64_t step = 0; step < T; ++step) {
-        const IndexSlot s = load_slot(slots, i);
-        ++*steps;
-        if (s.key == K) {
-            *out = s;
-            return true;
+    const uint64_t nb = T / kBucketSlots;
+    uint64_t b = home_bucket(K, T);
+    for (uint64_t step = 0; step < nb; ++step) {
+        const uint4* q = reinterpret_cast<const uint4*>(slots) + b * kBucketSlots;
+        uint4 v[kBucketSlots];
+#pragma unroll
+        for (int j = 0; j < kBucketSlots; ++j) v[j] = __ldg(q + j);
+        *steps += kBucketSlots;
+        bool empty = false;
+#pragma unroll
+        for (int j = 0; j < kBucketSlots; ++j) {
+            const unsigned long long key = ((unsigned long long)v[j].y << 32) | v[j].x;
+            if (key == K) {
+                out->key = key;
+                out->field = v[j].z;
+                out->nA = (uint16_t)(v[j].w & 0xffffu);
+                out->nB = (uint16_t)(v[j].w >> 16);
+                return true;
+            }
+            empty |= (key == kEmptyKey);
         }
-        if (s.key == kEmptyKey) return false;
-        i = (i + 1 == T) ? 0 : i + 1;
+        if (empty) return false;
+        b = (b + 1 == nb) ? 0 : b + 1;
     }
     atomicOr(status, kStProbeRunaway);
     return false;

@@ -15,7 +15,7 @@ struct Engine {
     std::mutex mu;
     cudaStream_t own_stream = nullptr;
     int sms = 0;
-    DevBuf stats, head, packed, gtab, ghits;
+    DevBuf stats, head, packed, gtab, ghits, heavy;
     DevBuf h_reads, h_offsets, h_out, h_dmax;  // device copies for the host-buffer entry points
     PinnedBuf pin;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -41,6 +41,14 @@ inline int grid_cap(int sms, uint64_t n, int threads) {
     if (want < 1) want = 1;
     return (int)want;
 }
+
+// thread-per-read bucket (snap_light.cu): limits of the reads it takes
+constexpr int kLightBucketMaxM = 128;
+constexpr int kLightBucketMaxSeeds = 6;
+constexpr int kLightBucketMaxL = 15;
+int launch_light(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
+                 const snap_params* p, snap_result* d_out, cudaStream_t stream,
+                 const BatchPrep& bp, uint32_t* heavy_ids, unsigned long long* heavy_count);
 
 int prepare_batch(const snap_index* idx, Engine* e, const uint8_t* d_reads,
                   const uint64_t* d_offsets, uint64_t n, const snap_params* p,

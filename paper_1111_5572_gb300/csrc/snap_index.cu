@@ -7,7 +7,9 @@
 // open-addressing table keyed by the canonical s-mer min(S, revcomp(S)) with
 // the two orientations kept as separate position lists (so a 32-bit position
 // never loses a bit to a strand flag), positions of keys seen once stored in
-// the slot itself.  Built count-then-fill with atomics; no sort.
+// the slot itself; slots are grouped in 64-byte buckets of four so that a
+// lookup is normally one DRAM access.  Built count-then-fill with atomics; no
+// sort.
 #include <chrono>
 #include <cstdio>
 
@@ -75,19 +77,23 @@ __global__ void k_insert(const uint32_t* __restrict__ words, uint64_t npos, int 
         uint64_t K;
         int o;
         canonical_at(words, l, s, &K, &o);
-        uint64_t i = home_slot(K, T);
+        const uint64_t nb = T / kBucketSlots;
+        uint64_t b = home_bucket(K, T);
         bool placed = false;
-        for (uint64_t step = 0; step < T; ++step) {
-            unsigned long long* kp = &slots[i].key;
-            unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(kp);
-            if (cur == kEmptyKey) cur = atomicCAS(kp, kEmptyKey, (unsigned long long)K);
-            if (cur == kEmptyKey || cur == K) {
-                uint32_t* cnt = reinterpret_cast<uint32_t*>(&slots[i].field) + o;
-                atomicAdd(cnt, 1u);
-                placed = true;
-                break;
+        for (uint64_t step = 0; step < nb && !placed; ++step) {
+            for (int j = 0; j < kBucketSlots; ++j) {
+                const uint64_t i = b * kBucketSlots + j;
+                unsigned long long* kp = &slots[i].key;
+                unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(kp);
+                if (cur == kEmptyKey) cur = atomicCAS(kp, kEmptyKey, (unsigned long long)K);
+                if (cur == kEmptyKey || cur == K) {
+                    uint32_t* cnt = reinterpret_cast<uint32_t*>(&slots[i].field) + o;
+                    atomicAdd(cnt, 1u);
+                    placed = true;
+                    break;
+                }
             }
-            i = (i + 1 == T) ? 0 : i + 1;
+            b = (b + 1 == nb) ? 0 : b + 1;
         }
         if (!placed) atomicOr(status, kStTableFull);
     }
@@ -136,24 +142,31 @@ __global__ void k_fill(const uint32_t* __restrict__ words, uint64_t npos, int s,
         int o;
         canonical_at(words, l, s, &K, &o);
         if (o != which) continue;
-        uint64_t i = home_slot(K, T);
-        bool found = false;
-        for (uint64_t step = 0; step < T; ++step) {
-            const uint4 v = reinterpret_cast<const uint4*>(slots)[i];
-            const uint64_t key = ((uint64_t)v.y << 32) | v.x;
-            if (key == K) {
-                const uint32_t tot = (v.w & 0xffffu) + (v.w >> 16);
-                if (tot == 1) {
-                    slots[i].field = (uint32_t)l;
-                } else if (tot <= kListMax) {
-                    const uint32_t at = atomicAdd(&cursor[i], 1u);
-                    positions[at] = (uint32_t)l;
+        const uint64_t nb = T / kBucketSlots;
+        uint64_t b = home_bucket(K, T);
+        bool found = false, ended = false;
+        for (uint64_t step = 0; step < nb && !found && !ended; ++step) {
+            for (int j = 0; j < kBucketSlots; ++j) {
+                const uint64_t i = b * kBucketSlots + j;
+                const uint4 v = reinterpret_cast<const uint4*>(slots)[i];
+                const uint64_t key = ((uint64_t)v.y << 32) | v.x;
+                if (key == K) {
+                    const uint32_t tot = (v.w & 0xffffu) + (v.w >> 16);
+                    if (tot == 1) {
+                        slots[i].field = (uint32_t)l;
+                    } else if (tot <= kListMax) {
+                        const uint32_t at = atomicAdd(&cursor[i], 1u);
+                        positions[at] = (uint32_t)l;
+                    }
+                    found = true;
+                    break;
                 }
-                found = true;
-                break;
+                if (key == kEmptyKey) {
+                    ended = true;
+                    break;
+                }
             }
-            if (key == kEmptyKey) break;
-            i = (i + 1 == T) ? 0 : i + 1;
+            b = (b + 1 == nb) ? 0 : b + 1;
         }
         if (!found) atomicOr(status, kStInternal);
     }
@@ -201,7 +214,7 @@ extern "C" int snap_index_build(const uint8_t* genome_ascii, uint64_t genome_len
     idx->G = genome_len;
     idx->s = seed_len;
     const uint64_t npos = genome_len - seed_len + 1;
-    idx->T = npos + npos / 2 + 64;  // load factor <= 2/3
+    idx->T = ((npos + npos / 2 + 64) + kBucketSlots - 1) / kBucketSlots * kBucketSlots;  // load <= 2/3
     idx->genome_words_n = (genome_len + 15) / 16 + 8;
 
     uint8_t* d_ascii = nullptr;

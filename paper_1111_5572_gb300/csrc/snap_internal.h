@@ -95,6 +95,7 @@ struct BatchStats {
     int status;
     unsigned long long max_hits_bound;  // max over reads of n * h_max (capped)
     DevCounters ctr;
+    unsigned long long n_light;  // reads short enough for the thread-per-read bucket
 };
 
 }  // namespace snapgpu

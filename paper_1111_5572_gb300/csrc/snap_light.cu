@@ -1,0 +1,380 @@
+// snap_light.cu — Algorithm 1 ("SNAP alignment algorithm") with one thread per
+// short read, the first length bucket of the batched form.
+//
+// A read is handled here when it is short (m <= 128), uses at most 6 seeds, has a
+// largest edit-distance limit d_max + c - 1 <= 15 and its non-popular seeds hit at
+// most 16 index positions; the thread then runs the whole per-read loop alone:
+// seed probes, votes in a small per-thread candidate list, the most-voted pick,
+// the limit schedule, a Landau-Vishkin edit distance over one diagonal at a time,
+// best / second best over 32-base buckets and the exits.  Any other read is
+// appended to a device list that the warp-per-read kernel (snap_align.cu) drains
+// next, so every read is aligned by exactly one of the two, with the same
+// readings of the paper (see snap_align.cu).
+//
+// Per-thread arrays live in shared memory in column order (word w of thread t at
+// w * blockDim + t) so that a warp's accesses to the same word fall in 32
+// different banks.
+#include <algorithm>
+#include <cstring>
+
+#include "snap_device.cuh"
+#include "snap_engine.h"
+#include "snap_internal.h"
+
+namespace snapgpu {
+
+constexpr int kLightThreads = 128;
+constexpr int kLightMaxM = kLightBucketMaxM;
+constexpr int kLightMaxSeeds = kLightBucketMaxSeeds;
+constexpr int kLightMaxL = kLightBucketMaxL;
+constexpr int kLightMaxCands = 16;
+constexpr int kLightXW = kLightMaxM / 16 + 2;                           // read words + 2
+constexpr int kLightTW = (15 + kLightMaxM + kLightMaxL + 15) / 16 + 2;  // window words
+constexpr int kLightRW = 2 * kLightMaxL + 3;                            // diagonals + 2
+constexpr int kLightWords = 2 * kLightXW + kLightTW + kLightRW;
+
+namespace {
+
+constexpr int kInfL = 1 << 28;
+
+struct LightArgs {
+    const uint32_t* genome;
+    uint64_t G;
+    int s;
+    const IndexSlot* slots;
+    uint64_t T;
+    const uint32_t* positions;
+    const uint32_t* rwords;
+    const uint64_t* offsets;
+    uint64_t base0;
+    uint64_t n;
+    int d_max, h_max, c, num_seeds;
+    const int32_t* dmax_per_read;
+    uint8_t shifts[32];
+    int n_shifts;
+    snap_result* out;
+    uint32_t* heavy_ids;
+    unsigned long long* heavy_count;
+    int* status;
+    DevCounters* ctr;
+};
+
+// 16 / 32 bases from a column-stored packed sequence
+__device__ __forceinline__ uint32_t col16(const uint32_t* col, int i) {
+    const int q = i >> 4;
+    return __funnelshift_r(col[q * kLightThreads], col[(q + 1) * kLightThreads],
+                           (uint32_t)(i & 15) * 2u);
+}
+__device__ __forceinline__ uint64_t col32(const uint32_t* col, int i) {
+    const int q = i >> 4;
+    const uint32_t sh = (uint32_t)(i & 15) * 2u;
+    const uint32_t w0 = col[q * kLightThreads], w1 = col[(q + 1) * kLightThreads],
+                   w2 = col[(q + 2) * kLightThreads];
+    return ((uint64_t)__funnelshift_r(w1, w2, sh) << 32) | __funnelshift_r(w0, w1, sh);
+}
+
+// Farthest reach per diagonal by one thread: rounds e = 0..L, diagonals k = -e..e
+// in increasing order updated in place (the old value of k-1 is carried).
+__device__ __forceinline__ int lv_thread(const uint32_t* X, int m, const uint32_t* Tw, int tb,
+                                         int n, int L, int* R) {
+    constexpr int NEG = -0x40000000;
+    if (L < 0) return kOver;
+    // R[k] holds round e-1's value only for |k| <= e-1; anything outside that
+    // range is read as "unreachable", so the array needs no initialisation
+    for (int e = 0; e <= L; ++e) {
+        int left_old = NEG;
+        for (int k = -e; k <= e; ++k) {
+            int* slot = R + (k + L + 1) * kLightThreads;
+            const int cur_old = (k >= -(e - 1) && k <= e - 1) ? *slot : NEG;
+            int r;
+            if (e == 0) {
+                r = 0;
+            } else {
+                const int right_old = (k + 1 <= e - 1) ? slot[kLightThreads] : NEG;
+                r = max(max(cur_old + 1, right_old + 1), left_old);
+            }
+            left_old = cur_old;
+            if (r > m) r = m;
+            if (r + k > n) r = n - k;
+            if (r < 0 || r + k < 0) {
+                *slot = NEG;
+                continue;
+            }
+            for (;;) {
+                const int lim = min(m - r, n - (r + k));
+                if (lim <= 0) break;
+                const uint32_t x = col16(X, r) ^ col16(Tw, tb + r + k);
+                const int adv = x ? ((__ffs(x) - 1) >> 1) : 16;
+                if (adv >= lim) {
+                    r += lim;
+                    break;
+                }
+                r += adv;
+                if (adv < 16) break;
+            }
+            *slot = r;
+            if (r >= m) return e;
+        }
+    }
+    return kOver;
+}
+
+__global__ void __launch_bounds__(kLightThreads) k_align_light(LightArgs a) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int tid = threadIdx.x;
+    uint32_t* Xf = smem + tid;
+    uint32_t* Xr = Xf + kLightXW * kLightThreads;
+    uint32_t* Tw = Xr + kLightXW * kLightThreads;
+    int* R = reinterpret_cast<int*>(Tw + kLightTW * kLightThreads);
+    const uint64_t r = blockIdx.x * (uint64_t)kLightThreads + tid;
+
+    uint32_t c_seeds = 0, c_slots = 0, c_list = 0, c_ed = 0, c_over = 0, c_words = 0;
+    if (r < a.n) {
+        const uint64_t o0 = a.offsets[r];
+        const int m = (int)(a.offsets[r + 1] - o0);
+        const int s = a.s;
+        int n = 0;
+        if (m >= s) {
+            n = a.num_seeds > 0 ? a.num_seeds : m / s;
+            n = min(n, m - s + 1);
+        }
+        const int dmax = a.dmax_per_read ? a.dmax_per_read[r] : a.d_max;
+        const int c = a.c;
+        bool heavy = m > kLightMaxM || n > kLightMaxSeeds || dmax + c - 1 > kLightMaxL;
+        long long res_loc = -1;
+        int res_d = -1, res_strand = 0, res_cls = SNAP_NOT_FOUND;
+        if (!heavy && n > 0) {
+            const uint64_t rb = o0 - a.base0 + kReadPadBases;
+            const int nw = (m + 15) / 16;
+            // the read's aligned packed words (one before, one after) go to the
+            // window column first; both strands are cut from them
+            const uint64_t q0 = rb >> 4;
+            const uint32_t sh = (uint32_t)(rb & 15) * 2u;
+            const uint64_t xe = rb + (uint64_t)m;
+            const int dq = (int)((xe >> 4) - q0);
+            const uint32_t shx = (uint32_t)(xe & 15) * 2u;
+            for (int j = 0; j <= nw + 1; ++j) Tw[j * kLightThreads] = a.rwords[q0 - 1 + j];
+#pragma unroll
+            for (int w = 0; w < kLightXW; ++w) {
+                uint32_t f = 0, rc = 0;
+                if (w < nw) {
+                    f = __funnelshift_r(Tw[(w + 1) * kLightThreads], Tw[(w + 2) * kLightThreads],
+                                        sh);
+                    rc = rev_groups32(~__funnelshift_r(Tw[(dq - w) * kLightThreads],
+                                                       Tw[(dq - w + 1) * kLightThreads], shx));
+                }
+                Xf[w * kLightThreads] = f;
+                Xr[w * kLightThreads] = rc;
+            }
+            // seed lookups
+            SeedRec seeds[kLightMaxSeeds];
+            unsigned H = 0;
+            for (int i = 0; i < n; ++i) {
+                bool p0 = false;
+                const int o = seed_offset(i, m, s, a.shifts, a.n_shifts, &p0);
+                SeedRec rec;
+                rec.flags = (uint8_t)(kSeedValid | (p0 ? kSeedPass0 : 0));
+                rec.offset = (uint16_t)o;
+                rec.pad = 0;
+                const uint64_t v = col32(Xf, o) & kmer_mask(s);
+                uint32_t cnt = 0;
+                lookup_seed(a.slots, a.T, a.positions, v, s, &rec, &cnt, a.status, &c_slots);
+                ++c_seeds;
+                if (cnt > (uint32_t)a.h_max) {
+                    rec.flags |= kSeedPopular;
+                } else {
+                    H += (unsigned)rec.fwd_n + rec.rc_n;
+                }
+                seeds[i] = rec;
+            }
+            heavy = H > (unsigned)kLightMaxCands;
+            if (!heavy) {
+                unsigned long long ckey[kLightMaxCands];
+                uint8_t cvotes[kLightMaxCands];
+                int8_t cstate[kLightMaxCands];
+                unsigned long long hkey[kLightMaxCands];
+                int8_t hd[kLightMaxCands];
+                int nc = 0, nh = 0, t = 0;
+                int d_best = kInfL, d_second = kInfL;
+                unsigned long long best_key = 0;
+                bool any_nonpopular = false, returned = false, draining = false;
+                int i = 0;
+                for (;;) {
+                    if (!draining) {
+                        while (i < n && (seeds[i].flags & kSeedPopular)) ++i;
+                        if (i >= n) break;
+                        const SeedRec rec = seeds[i++];
+                        any_nonpopular = true;
+                        const int o = rec.offset;
+                        const int tot = (int)rec.fwd_n + rec.rc_n;
+                        for (int j = 0; j < tot; ++j) {
+                            const bool fwd = j < rec.fwd_n;
+                            uint32_t l;
+                            if (rec.flags & kSeedFwdInline) {
+                                l = fwd ? rec.fwd_ref : rec.rc_ref;
+                            } else {
+                                l = fwd ? __ldg(a.positions + rec.fwd_ref + j)
+                                        : __ldg(a.positions + rec.rc_ref + (j - rec.fwd_n));
+                                ++c_list;
+                            }
+                            const long long p =
+                                fwd ? (long long)l - o : (long long)l - (m - o - s);
+                            if (p < 0) continue;
+                            const unsigned long long key =
+                                2ull * (unsigned long long)p + (fwd ? 0 : 1);
+                            int q = 0;
+                            while (q < nc && ckey[q] != key) ++q;
+                            if (q == nc) {
+                                ckey[nc] = key;
+                                cvotes[nc] = 0;
+                                cstate[nc] = (int8_t)kUnscored;
+                                ++nc;
+                            }
+                            ++cvotes[q];
+                        }
+                        if (rec.flags & kSeedPass0) ++t;
+                    }
+                    // most-voted unscored candidate, ties to the smaller key
+                    int pick = -1;
+                    for (int q = 0; q < nc; ++q) {
+                        if (cstate[q] != kUnscored) continue;
+                        if (pick < 0 || cvotes[q] > cvotes[pick] ||
+                            (cvotes[q] == cvotes[pick] && ckey[q] < ckey[pick]))
+                            pick = q;
+                    }
+                    if (pick >= 0) {
+                        int L;
+                        if (d_best > dmax) {
+                            L = dmax + c - 1;
+                        } else if (d_second >= d_best + c) {
+                            L = d_best + c - 1;
+                        } else {
+                            L = d_best - 1;
+                        }
+                        const unsigned long long key = ckey[pick];
+                        int d = kOver;
+                        if (L >= 0) {
+                            const uint64_t p = key >> 1;
+                            const int n_t = (int)min(a.G - p, (uint64_t)(m + L));
+                            const uint64_t w0 = p >> 4;
+                            const int tb = (int)(p & 15);
+                            const int nwt = (tb + n_t + 15) / 16 + 2;
+                            for (int w = 0; w < nwt; ++w)
+                                Tw[w * kLightThreads] = __ldg(a.genome + w0 + w);
+                            c_words += nwt;
+                            d = lv_thread((key & 1) ? Xr : Xf, m, Tw, tb, n_t, L, R);
+                        }
+                        ++c_ed;
+                        c_over += (d < 0);
+                        cstate[pick] = (int8_t)(d >= 0 ? d : kOver);
+                        if (d >= 0) {
+                            hkey[nh] = key;
+                            hd[nh] = (int8_t)d;
+                            ++nh;
+                            const unsigned long long bk = ((key >> 6) << 1) | (key & 1);
+                            if (d < d_best) {
+                                d_best = d;
+                                best_key = key;
+                                d_second = kInfL;
+                                for (int q = 0; q < nh; ++q) {
+                                    const unsigned long long hb =
+                                        ((hkey[q] >> 6) << 1) | (hkey[q] & 1);
+                                    if (hb != bk) d_second = min(d_second, (int)hd[q]);
+                                }
+                            } else if (bk != (((best_key >> 6) << 1) | (best_key & 1))) {
+                                d_second = min(d_second, d);
+                            }
+                        }
+                    } else if (draining) {
+                        break;
+                    }
+                    if (!draining) {
+                        if (d_best < c && d_second < d_best + c) {
+                            returned = true;
+                            break;
+                        }
+                        if (t >= d_best + c) draining = true;
+                    }
+                }
+                if (!returned && d_best <= dmax && d_second >= d_best + c) {
+                    res_cls = SNAP_SINGLE_HIT;
+                } else if (returned || d_best <= dmax || !any_nonpopular) {
+                    res_cls = SNAP_MULTIPLE_HITS;
+                } else {
+                    res_cls = SNAP_NOT_FOUND;
+                }
+                if (res_cls != SNAP_NOT_FOUND && d_best <= dmax) {
+                    res_loc = (long long)(best_key >> 1);
+                    res_strand = (int)(best_key & 1);
+                    res_d = d_best;
+                }
+            }
+        }
+        if (heavy) {
+            const unsigned long long at = atomicAdd(a.heavy_count, 1ull);
+            a.heavy_ids[at] = (uint32_t)r;
+        } else {
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.out + r);
+            dst[0] = (unsigned long long)res_loc;
+            dst[1] = (unsigned long long)(uint32_t)res_d |
+                     ((unsigned long long)((uint32_t)res_strand | ((uint32_t)res_cls << 8))
+                      << 32);
+        }
+    }
+    unsigned long long v[6] = {c_seeds, c_slots, c_list, c_ed, c_over, c_words};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
+    }
+    if ((tid & 31) == 0) {
+        unsigned long long* dst = &a.ctr->seeds;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (v[k]) atomicAdd(dst + k, v[k]);
+    }
+}
+
+}  // namespace
+
+// Launch the thread-per-read bucket over all n reads; reads it does not take
+// are appended to heavy_ids (count in *heavy_count, cleared here).
+int launch_light(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
+                 const snap_params* p, snap_result* d_out, cudaStream_t stream,
+                 const BatchPrep& bp, uint32_t* heavy_ids, unsigned long long* heavy_count) {
+    LightArgs a;
+    memset(&a, 0, sizeof(a));
+    a.genome = idx->genome_words;
+    a.G = idx->G;
+    a.s = idx->s;
+    a.slots = idx->slots;
+    a.T = idx->T;
+    a.positions = idx->positions;
+    a.rwords = bp.rwords;
+    a.offsets = d_offsets;
+    a.base0 = bp.base0;
+    a.n = n;
+    a.d_max = p->max_dist;
+    a.h_max = p->max_hits;
+    a.c = p->conf_diff;
+    a.num_seeds = p->num_seeds;
+    a.dmax_per_read = p->max_dist_per_read;
+    shift_list(idx->s, a.shifts, &a.n_shifts);
+    a.out = d_out;
+    a.heavy_ids = heavy_ids;
+    a.heavy_count = heavy_count;
+    BatchStats* d_st = static_cast<BatchStats*>(e->stats.p);
+    a.status = &d_st->status;
+    a.ctr = &d_st->ctr;
+    const size_t smem = (size_t)kLightWords * kLightThreads * 4;
+    static_assert((size_t)kLightWords * kLightThreads * 4 <= 48 * 1024,
+                  "light bucket fits the default shared-memory limit");
+    SNAP_CUDA(cudaMemsetAsync(heavy_count, 0, sizeof(unsigned long long), stream), "clear");
+    const uint64_t blocks = (n + kLightThreads - 1) / kLightThreads;
+    e->launches++;
+    k_align_light<<<(unsigned)blocks, kLightThreads, smem, stream>>>(a);
+    SNAP_CUDA(cudaGetLastError(), "light launch");
+    return SNAP_OK;
+}
+
+}  // namespace snapgpu
