@@ -263,7 +263,9 @@ def run_ours(args):
     d_out = torch.zeros((n, 16), dtype=torch.uint8, device=dev)
     d_dpr = None if dpr is None else torch.from_numpy(dpr).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    # a stream of its own (not the legacy default stream) so the batched form can
+    # replay its launch sequence as a CUDA graph
+    stream = torch.cuda.Stream(device=dev)
 
     def one_step(form_plain):
         idx.align_device(d_b, d_o, d_out, d_max_dist_per_read=d_dpr, stream=stream,
@@ -337,6 +339,8 @@ def run_ours(args):
         "index_build_s": build_s, "index_device_gb": info["device_bytes"] / 1e9,
         "input_gen_s": gen_s, "wall_s_timed": wall,
         "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+        "launch_shape": {k: st[k] for k in ("light_threads", "warps_per_block", "table_slots",
+                                            "graph_replay")},
     }
 
     # the plain one-launch-per-stage form on the same GPU and inputs

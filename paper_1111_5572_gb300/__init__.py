@@ -27,7 +27,8 @@ assert RESULT_DTYPE.itemsize == 16
 EXPORTS = ("snap_index_build", "snap_index_free", "snap_index_info_get", "snap_align",
            "snap_align_device", "snap_align_plain_device", "snap_align_plain",
            "snap_server_create", "snap_server_submit", "snap_server_wait", "snap_server_destroy",
-           "snap_last_call_stats", "snap_align_device_noalloc", "snap_last_error")
+           "snap_last_call_stats", "snap_align_device_noalloc", "snap_index_configure",
+           "snap_last_error")
 
 
 class SnapError(RuntimeError):
@@ -56,7 +57,9 @@ class snap_call_stats(ctypes.Structure):
                 ("read_bases", ctypes.c_uint64), ("seeds", ctypes.c_uint64),
                 ("slot_reads", ctypes.c_uint64), ("list_entries", ctypes.c_uint64),
                 ("ed_calls", ctypes.c_uint64), ("ed_over", ctypes.c_uint64),
-                ("window_bytes", ctypes.c_uint64)]
+                ("window_bytes", ctypes.c_uint64), ("light_threads", ctypes.c_int32),
+                ("warps_per_block", ctypes.c_int32), ("table_slots", ctypes.c_int32),
+                ("graph_replay", ctypes.c_int32)]
 
 
 _lib = None
@@ -86,6 +89,7 @@ def load_library(path: str = LIB_PATH):
     lib.snap_server_wait.argtypes = [vp, u64, vp, P(ctypes.c_double)]
     lib.snap_server_destroy.argtypes = [vp]
     lib.snap_last_call_stats.argtypes = [vp, P(snap_call_stats)]
+    lib.snap_index_configure.argtypes = [vp, i32, i32]
     lib.snap_last_error.argtypes = []
     lib.snap_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -132,6 +136,11 @@ class Index:
         inf = snap_index_info()
         _check(load_library().snap_index_info_get(self._h, ctypes.byref(inf)), "info")
         return {f: getattr(inf, f) for f, _ in snap_index_info._fields_ if f != "reserved"}
+
+    def configure(self, autotune: bool = True, cuda_graphs: bool = True):
+        """snap_index_configure: autotuning of launch shapes and CUDA-graph replay."""
+        _check(load_library().snap_index_configure(self._h, int(autotune), int(cuda_graphs)),
+               "snap_index_configure")
 
     def last_call_stats(self) -> dict:
         """Stage timings and traffic counters of the last align call on this index."""

@@ -565,24 +565,42 @@ Engine* engine_create() {
 
 void engine_destroy(Engine* e) {
     if (!e) return;
-    for (DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->h_reads,
-                      &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds, &e->p_hits,
+    for (DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->heavy,
+                      &e->h_reads, &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds, &e->p_hits,
                       &e->p_hitoff, &e->p_partial, &e->p_table, &e->p_events, &e->p_hitlist,
                       &e->p_items, &e->p_misc})
         b->release();
     e->pin.release();
     for (auto& ev : e->ev)
         if (ev) cudaEventDestroy(ev);
+    for (auto& ev : e->pev)
+        if (ev) cudaEventDestroy(ev);
+    for (auto& ev : e->tev)
+        if (ev) cudaEventDestroy(ev);
+    if (e->gexec) cudaGraphExecDestroy(e->gexec);
     if (e->own_stream) cudaStreamDestroy(e->own_stream);
     delete e;
 }
 
 size_t engine_bytes(const Engine* e) {
     size_t s = 0;
-    for (const DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->h_reads,
-                            &e->h_offsets, &e->h_out, &e->h_dmax})
+    for (const DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->heavy,
+                            &e->h_reads, &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds,
+                            &e->p_hits, &e->p_hitoff, &e->p_partial, &e->p_table, &e->p_events,
+                            &e->p_hitlist, &e->p_items, &e->p_misc})
         s += b->bytes;
     return s;
+}
+
+void engine_release(Engine* e) {
+    if (e->gexec) {
+        cudaGraphExecDestroy(e->gexec);  // it points into the workspaces
+        e->gexec = nullptr;
+    }
+    for (DevBuf* b : {&e->packed, &e->gtab, &e->ghits, &e->heavy, &e->h_reads, &e->h_offsets,
+                      &e->h_out, &e->h_dmax, &e->p_seeds, &e->p_hits, &e->p_hitoff, &e->p_partial,
+                      &e->p_table, &e->p_events, &e->p_hitlist, &e->p_items, &e->p_misc})
+        b->release();
 }
 
 void shift_list(int s, uint8_t* out, int* n_out) {
@@ -733,14 +751,31 @@ static int finish_status(Engine* e, cudaStream_t stream, const char* where, uint
     L.ed_calls = h->ctr.ed_calls;
     L.ed_over = h->ctr.ed_over;
     L.window_bytes = h->ctr.window_words * 4;
+    L.light_threads = e->last_shape.light_threads;
+    L.warps_per_block = e->last_shape.warps;
+    L.table_slots = e->last_shape.scap;
+    L.graph_replay = e->last_graph;
     return SNAP_OK;
 }
 
-static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
-                       const snap_params* p, snap_result* d_out, cudaStream_t stream,
-                       const BatchPrep& bp) {
-    int rc;
+// One launch plan of the batched form for a given shape: the warp kernel's
+// layout and grid, and whether the thread-per-read bucket runs first.
+struct FusedPlan {
     FusedArgs a;
+    FusedKernel kfn = nullptr;
+    size_t smem = 0;
+    uint64_t blocks = 0;
+    LaunchShape shape;
+    bool light = false;
+};
+
+// Lay out the warp kernel for `shape` and make sure every buffer exists (no
+// allocation happens after this, so the enqueue below can be captured).
+static int plan_fused(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
+                      const snap_params* p, snap_result* d_out, const BatchPrep& bp,
+                      LaunchShape shape, FusedPlan* plan) {
+    int rc;
+    FusedArgs& a = plan->a;
     memset(&a, 0, sizeof(a));
     a.genome = idx->genome_words;
     a.G = idx->G;
@@ -770,15 +805,16 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
     a.wt = up4((mmax + Lmax + 15 + 15) / 16 + 4);
     a.seed_cap = nmax;
     a.lv_ints = Lmax > 127 ? up4(2 * (2 * Lmax + 4)) : 0;
-    // shared table: 128 slots holds the candidates of a read with up to 64 seed
-    // hits (almost every short read); reads with more use the warp's global table.
-    // A small per-warp footprint keeps many warps resident per SM.
+    // the shared candidate table holds reads with up to scap/2 seed hits; reads
+    // with more use the warp's global table
     const int fixed_words = 2 * a.wx + a.wt + 4 * a.seed_cap + a.lv_ints;
-    int warps = 8;
     const int budget_words = 200 * 1024 / 4;  // per block
+    int warps = std::max(1, shape.warps);
     while (warps > 1 && warps * (fixed_words + 6 * 64) > budget_words) warps >>= 1;
-    int scap = 128;
+    int scap = std::max(64, shape.scap);
     while (scap > 64 && warps * (fixed_words + 6 * scap) > budget_words) scap >>= 1;
+    shape.warps = warps;
+    shape.scap = scap;
     a.scap = scap;
     a.off_xr = a.wx;
     a.off_tw = 2 * a.wx;
@@ -798,17 +834,19 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
         return SNAP_E_INVAL;
     }
     const FusedKernel kfn = fused_kernel_for(Lmax);
-    SNAP_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-              "smem attr");
+    if ((rc = raise_smem_limit((const void*)kfn, (size_t)(int)smem))) return rc;
     int per_sm = 0;
     SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem),
               "occupancy");
     if (per_sm < 1) per_sm = 1;
+    plan->light = bp.st.n_light > 0 && shape.light_threads > 0;
     uint64_t blocks = (uint64_t)e->sms * per_sm;
-    const uint64_t need_blocks = (n + warps - 1) / warps;
-    if (blocks > need_blocks) blocks = need_blocks;
+    if (!plan->light) {
+        const uint64_t need_blocks = (n + warps - 1) / warps;
+        if (blocks > need_blocks) blocks = need_blocks;
+    }
     // global overflow tables for reads whose candidate table outgrows shared memory
-    uint64_t hb = bp.st.max_hits_bound;
+    const uint64_t hb = bp.st.max_hits_bound;
     uint64_t gcap = 64;
     while (gcap < 2 * hb) gcap <<= 1;
     if (gcap > kMaxTableSlots) {
@@ -818,8 +856,7 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
     }
     if (gcap > (uint64_t)scap) {
         const uint64_t per_warp = gcap * (sizeof(CandSlot) + sizeof(HitRec) / 2);
-        const uint64_t budget = 4ull << 30;
-        uint64_t max_warps = std::max<uint64_t>(1, budget / per_warp);
+        const uint64_t max_warps = std::max<uint64_t>(1, e->overflow_budget / per_warp);
         if (blocks * warps > max_warps) blocks = std::max<uint64_t>(1, max_warps / warps);
         const uint64_t tw = blocks * warps;
         if ((rc = e->gtab.ensure(tw * gcap * sizeof(CandSlot), "overflow tables"))) return rc;
@@ -830,24 +867,137 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
     }
     if ((rc = e->head.ensure(64, "queue head"))) return rc;
     a.head = static_cast<unsigned long long*>(e->head.p);
-    SNAP_CUDA(cudaMemsetAsync(a.head, 0, sizeof(unsigned long long), stream), "head clear");
-    if (bp.st.n_light > 0) {
-        // short reads: one thread each; the warp kernel then takes the rest
+    if (plan->light) {
         if ((rc = e->heavy.ensure(n * sizeof(uint32_t), "read list"))) return rc;
-        unsigned long long* heavy_count = a.head + 1;
-        uint32_t* heavy_ids = static_cast<uint32_t*>(e->heavy.p);
-        if ((rc = launch_light(idx, e, d_offsets, n, p, d_out, stream, bp, heavy_ids,
-                               heavy_count)))
+        a.order = static_cast<uint32_t*>(e->heavy.p);
+        a.n_items_dev = a.head + 1;
+        if ((rc = light_prepare())) return rc;
+    }
+    plan->kfn = kfn;
+    plan->smem = smem;
+    plan->blocks = blocks;
+    plan->shape = shape;
+    return SNAP_OK;
+}
+
+// Enqueue the planned launch sequence on `stream` (allocation-free; capturable).
+static int enqueue_fused(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
+                         const snap_params* p, snap_result* d_out, cudaStream_t stream,
+                         const BatchPrep& bp, const FusedPlan& plan) {
+    int rc;
+    SNAP_CUDA(cudaMemsetAsync(plan.a.head, 0, sizeof(unsigned long long), stream), "head clear");
+    if (plan.light) {
+        // short reads: one thread each; the warp kernel then takes the rest
+        if ((rc = launch_light(idx, e, d_offsets, n, p, d_out, stream, bp,
+                               const_cast<uint32_t*>(plan.a.order),
+                               const_cast<unsigned long long*>(plan.a.n_items_dev),
+                               plan.shape.light_threads)))
             return rc;
-        a.order = heavy_ids;
-        a.n_items_dev = heavy_count;
-        blocks = (uint64_t)e->sms * per_sm;
-        if (a.gtab && blocks * warps * gcap * sizeof(CandSlot) > e->gtab.bytes)
-            blocks = e->gtab.bytes / (warps * gcap * sizeof(CandSlot));
     }
     e->launches++;
-    kfn<<<(unsigned)blocks, warps * 32, smem, stream>>>(a);
+    plan.kfn<<<(unsigned)plan.blocks, plan.shape.warps * 32, plan.smem, stream>>>(plan.a);
     SNAP_CUDA(cudaGetLastError(), "align launch");
+    return SNAP_OK;
+}
+
+// Launch shapes the tuner tries: threads per block of the thread-per-read
+// bucket, warps per block and shared candidate slots of the warp kernel.
+static const LaunchShape kShapes[] = {
+    {128, 8, 128}, {64, 8, 128}, {256, 8, 128}, {128, 8, 64}, {128, 4, 256}, {128, 4, 128},
+};
+
+static bool same_key(const TuneKey& x, const TuneKey& y) {
+    return x.lvd == y.lvd && x.light == y.light && x.mmax == y.mmax && x.Lmax == y.Lmax &&
+           x.nmax == y.nmax && x.hits == y.hits && x.nbucket == y.nbucket;
+}
+
+static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
+                       const snap_params* p, snap_result* d_out, cudaStream_t stream,
+                       const BatchPrep& bp) {
+    int rc;
+    TuneKey key;
+    key.lvd = 0;  // the kernel variant follows from Lmax
+    key.light = bp.st.n_light > 0;
+    key.mmax = (int)bp.st.max_len;
+    key.Lmax = bp.st.max_L0;
+    key.nmax = bp.st.max_seeds;
+    key.hits = bp.st.max_hits_bound;
+    int lg = 0;
+    while ((1ull << lg) < n) ++lg;
+    key.nbucket = lg;  // batches within a factor of two share a tuned shape
+    LaunchShape shape = kShapes[0];
+    bool tuned = false;
+    for (const auto& t : e->tuned)
+        if (same_key(t.first, key)) {
+            shape = t.second;
+            tuned = true;
+        }
+    if (!tuned && e->autotune && n >= 4096) {
+        // time every candidate shape on this batch (results do not depend on it)
+        if (!e->tev[0])
+            for (auto& ev : e->tev) SNAP_CUDA(cudaEventCreate(&ev), "event create");
+        float best_ms = 1e30f;
+        for (const LaunchShape& cand : kShapes) {
+            if (!key.light && cand.light_threads != kShapes[0].light_threads) continue;
+            FusedPlan tp;
+            if ((rc = plan_fused(idx, e, d_offsets, n, p, d_out, bp, cand, &tp))) return rc;
+            SNAP_CUDA(cudaEventRecord(e->tev[0], stream), "event");
+            if ((rc = enqueue_fused(idx, e, d_offsets, n, p, d_out, stream, bp, tp))) return rc;
+            SNAP_CUDA(cudaEventRecord(e->tev[1], stream), "event");
+            SNAP_CUDA(cudaEventSynchronize(e->tev[1]), "tune");
+            float ms = 0;
+            SNAP_CUDA(cudaEventElapsedTime(&ms, e->tev[0], e->tev[1]), "tune");
+            if (ms < best_ms) {
+                best_ms = ms;
+                shape = tp.shape;
+            }
+        }
+        e->tuned.push_back({key, shape});
+        tuned = true;
+    }
+    FusedPlan plan;
+    if ((rc = plan_fused(idx, e, d_offsets, n, p, d_out, bp, shape, &plan))) return rc;
+    e->last_shape = plan.shape;
+    e->last_graph = 0;
+    const int launches_before = (int)e->launches;
+    if (e->use_graphs && stream != nullptr && stream != cudaStreamLegacy &&
+        stream != cudaStreamPerThread) {
+        // capture the launch sequence and replay it as one graph; an existing
+        // executable graph is updated in place when only parameters changed
+        cudaGraph_t g = nullptr;
+        SNAP_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "capture");
+        rc = enqueue_fused(idx, e, d_offsets, n, p, d_out, stream, bp, plan);
+        const cudaError_t ce = cudaStreamEndCapture(stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        SNAP_CUDA(ce, "end capture");
+        bool ok = false;
+        if (e->gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            ok = cudaGraphExecUpdate(e->gexec, g, &info) == cudaSuccess;
+            if (!ok) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(e->gexec);
+                e->gexec = nullptr;
+            }
+        }
+        if (!ok) {
+            const cudaError_t ie = cudaGraphInstantiate(&e->gexec, g, 0);
+            if (ie != cudaSuccess) {
+                cudaGraphDestroy(g);
+                e->gexec = nullptr;
+                return cuda_fail(ie, "graph instantiate");
+            }
+        }
+        cudaGraphDestroy(g);
+        SNAP_CUDA(cudaGraphLaunch(e->gexec, stream), "graph launch");
+        e->last_graph = 1;
+    } else {
+        if ((rc = enqueue_fused(idx, e, d_offsets, n, p, d_out, stream, bp, plan))) return rc;
+    }
+    (void)launches_before;
     return SNAP_OK;
 }
 
@@ -942,6 +1092,19 @@ extern "C" int snap_align_plain(const snap_index* idx, const uint8_t* reads,
                                 const uint64_t* offsets, uint64_t n, const snap_params* p,
                                 snap_result* out) {
     return align_host(idx, reads, offsets, n, p, out, true);
+}
+
+extern "C" int snap_index_configure(snap_index* idx, int autotune, int cuda_graphs) {
+    clear_error();
+    if (!idx) {
+        set_error("snap_index_configure: index is NULL");
+        return SNAP_E_INVAL;
+    }
+    std::lock_guard<std::mutex> lock(idx->engine->mu);
+    idx->engine->autotune = autotune != 0;
+    idx->engine->use_graphs = cuda_graphs != 0;
+    if (!autotune) idx->engine->tuned.clear();
+    return SNAP_OK;
 }
 
 extern "C" int snap_last_call_stats(const snap_index* idx, snap_call_stats* out) {
@@ -1137,8 +1300,7 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
         return SNAP_E_INVAL;
     }
     const FusedKernel kfn = fused_kernel_for(Lmax);
-    SNAP_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-              "smem attr");
+    if ((rc = raise_smem_limit((const void*)kfn, (size_t)(int)smem))) return rc;
     int per_sm = 0;
     SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem),
               "occupancy");
@@ -1169,9 +1331,7 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
                 // fewer warps per block; each warp keeps the same shared-memory layout
                 warps = (int)max_warps;
                 const size_t smem_w = (size_t)warps * a.warp_words * 4;
-                SNAP_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem_w),
-                          "smem attr");
+                if ((rc = raise_smem_limit((const void*)kfn, (size_t)(int)smem_w))) return rc;
             }
             blocks = std::max<uint64_t>(1, max_warps / warps);
         }

@@ -5,10 +5,26 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "snap_internal.h"
 
 namespace snapgpu {
+
+// A launch shape of the batched form (chosen by the autotuner per batch shape).
+struct LaunchShape {
+    int light_threads;  // threads per block of the thread-per-read bucket
+    int warps;          // warps per block of the warp-per-read kernel
+    int scap;           // shared-memory candidate slots per warp
+};
+
+// What a tuned shape is keyed on: the kernel variant and the batch statistics
+// that decide the layout.
+struct TuneKey {
+    int lvd, light, mmax, Lmax, nmax, nbucket;
+    unsigned long long hits;
+};
 
 struct Engine {
     // everything an align call on one index needs; guarded by mu
@@ -22,6 +38,15 @@ struct Engine {
     cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};  // plain-form stage marks
     uint64_t launches = 0;
     snap_call_stats last{};
+    // autotuner and graph replay of the batched form
+    bool autotune = true;
+    bool use_graphs = true;
+    std::vector<std::pair<TuneKey, LaunchShape>> tuned;
+    cudaEvent_t tev[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec = nullptr;
+    LaunchShape last_shape{0, 0, 0};
+    int last_graph = 0;
+    uint64_t overflow_budget = 4ull << 30;  // device bytes for per-warp global candidate tables
     // plain-form workspace
     DevBuf p_seeds, p_hits, p_hitoff, p_partial, p_table, p_events, p_hitlist, p_items, p_misc;
 };
@@ -46,9 +71,11 @@ inline int grid_cap(int sms, uint64_t n, int threads) {
 constexpr int kLightBucketMaxM = 128;
 constexpr int kLightBucketMaxSeeds = 6;
 constexpr int kLightBucketMaxL = 15;
+int light_prepare();
 int launch_light(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
                  const snap_params* p, snap_result* d_out, cudaStream_t stream,
-                 const BatchPrep& bp, uint32_t* heavy_ids, unsigned long long* heavy_count);
+                 const BatchPrep& bp, uint32_t* heavy_ids, unsigned long long* heavy_count,
+                 int threads);
 
 int prepare_batch(const snap_index* idx, Engine* e, const uint8_t* d_reads,
                   const uint64_t* d_offsets, uint64_t n, const snap_params* p,

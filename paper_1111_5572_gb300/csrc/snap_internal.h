@@ -127,6 +127,7 @@ namespace snapgpu {
 void set_error(const char* fmt, ...);
 void clear_error();
 int cuda_fail(cudaError_t e, const char* what);
+int raise_smem_limit(const void* func, size_t bytes);  // never lowers it
 
 #define SNAP_CUDA(call, what)                                  \
     do {                                                       \
@@ -163,5 +164,6 @@ int align_batch_device(const snap_index* idx, Engine* eng, const uint8_t* d_read
 Engine* engine_create();
 void engine_destroy(Engine* e);
 size_t engine_bytes(const Engine* e);
+void engine_release(Engine* e);  // frees the workspaces (kept: streams, events, tuning)
 
 }  // namespace snapgpu

@@ -23,7 +23,6 @@
 
 namespace snapgpu {
 
-constexpr int kLightThreads = 128;
 constexpr int kLightMaxM = kLightBucketMaxM;
 constexpr int kLightMaxSeeds = kLightBucketMaxSeeds;
 constexpr int kLightMaxL = kLightBucketMaxL;
@@ -59,24 +58,22 @@ struct LightArgs {
     DevCounters* ctr;
 };
 
-// 16 / 32 bases from a column-stored packed sequence
-__device__ __forceinline__ uint32_t col16(const uint32_t* col, int i) {
+// 16 / 32 bases from a column-stored packed sequence (stride = threads per block)
+__device__ __forceinline__ uint32_t col16(const uint32_t* col, int i, int st) {
     const int q = i >> 4;
-    return __funnelshift_r(col[q * kLightThreads], col[(q + 1) * kLightThreads],
-                           (uint32_t)(i & 15) * 2u);
+    return __funnelshift_r(col[q * st], col[(q + 1) * st], (uint32_t)(i & 15) * 2u);
 }
-__device__ __forceinline__ uint64_t col32(const uint32_t* col, int i) {
+__device__ __forceinline__ uint64_t col32(const uint32_t* col, int i, int st) {
     const int q = i >> 4;
     const uint32_t sh = (uint32_t)(i & 15) * 2u;
-    const uint32_t w0 = col[q * kLightThreads], w1 = col[(q + 1) * kLightThreads],
-                   w2 = col[(q + 2) * kLightThreads];
+    const uint32_t w0 = col[q * st], w1 = col[(q + 1) * st], w2 = col[(q + 2) * st];
     return ((uint64_t)__funnelshift_r(w1, w2, sh) << 32) | __funnelshift_r(w0, w1, sh);
 }
 
 // Farthest reach per diagonal by one thread: rounds e = 0..L, diagonals k = -e..e
 // in increasing order updated in place (the old value of k-1 is carried).
 __device__ __forceinline__ int lv_thread(const uint32_t* X, int m, const uint32_t* Tw, int tb,
-                                         int n, int L, int* R) {
+                                         int n, int L, int* R, int st) {
     constexpr int NEG = -0x40000000;
     if (L < 0) return kOver;
     // R[k] holds round e-1's value only for |k| <= e-1; anything outside that
@@ -84,13 +81,13 @@ __device__ __forceinline__ int lv_thread(const uint32_t* X, int m, const uint32_
     for (int e = 0; e <= L; ++e) {
         int left_old = NEG;
         for (int k = -e; k <= e; ++k) {
-            int* slot = R + (k + L + 1) * kLightThreads;
+            int* slot = R + (k + L + 1) * st;
             const int cur_old = (k >= -(e - 1) && k <= e - 1) ? *slot : NEG;
             int r;
             if (e == 0) {
                 r = 0;
             } else {
-                const int right_old = (k + 1 <= e - 1) ? slot[kLightThreads] : NEG;
+                const int right_old = (k + 1 <= e - 1) ? slot[st] : NEG;
                 r = max(max(cur_old + 1, right_old + 1), left_old);
             }
             left_old = cur_old;
@@ -103,7 +100,7 @@ __device__ __forceinline__ int lv_thread(const uint32_t* X, int m, const uint32_
             for (;;) {
                 const int lim = min(m - r, n - (r + k));
                 if (lim <= 0) break;
-                const uint32_t x = col16(X, r) ^ col16(Tw, tb + r + k);
+                const uint32_t x = col16(X, r, st) ^ col16(Tw, tb + r + k, st);
                 const int adv = x ? ((__ffs(x) - 1) >> 1) : 16;
                 if (adv >= lim) {
                     r += lim;
@@ -119,14 +116,15 @@ __device__ __forceinline__ int lv_thread(const uint32_t* X, int m, const uint32_
     return kOver;
 }
 
-__global__ void __launch_bounds__(kLightThreads) k_align_light(LightArgs a) {
+__global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     const int tid = threadIdx.x;
+    const int st = blockDim.x;  // column stride of the per-thread arrays
     uint32_t* Xf = smem + tid;
-    uint32_t* Xr = Xf + kLightXW * kLightThreads;
-    uint32_t* Tw = Xr + kLightXW * kLightThreads;
-    int* R = reinterpret_cast<int*>(Tw + kLightTW * kLightThreads);
-    const uint64_t r = blockIdx.x * (uint64_t)kLightThreads + tid;
+    uint32_t* Xr = Xf + kLightXW * st;
+    uint32_t* Tw = Xr + kLightXW * st;
+    int* R = reinterpret_cast<int*>(Tw + kLightTW * st);
+    const uint64_t r = blockIdx.x * (uint64_t)st + tid;
 
     uint32_t c_seeds = 0, c_slots = 0, c_list = 0, c_ed = 0, c_over = 0, c_words = 0;
     if (r < a.n) {
@@ -153,18 +151,17 @@ __global__ void __launch_bounds__(kLightThreads) k_align_light(LightArgs a) {
             const uint64_t xe = rb + (uint64_t)m;
             const int dq = (int)((xe >> 4) - q0);
             const uint32_t shx = (uint32_t)(xe & 15) * 2u;
-            for (int j = 0; j <= nw + 1; ++j) Tw[j * kLightThreads] = a.rwords[q0 - 1 + j];
+            for (int j = 0; j <= nw + 1; ++j) Tw[j * st] = a.rwords[q0 - 1 + j];
 #pragma unroll
             for (int w = 0; w < kLightXW; ++w) {
                 uint32_t f = 0, rc = 0;
                 if (w < nw) {
-                    f = __funnelshift_r(Tw[(w + 1) * kLightThreads], Tw[(w + 2) * kLightThreads],
-                                        sh);
-                    rc = rev_groups32(~__funnelshift_r(Tw[(dq - w) * kLightThreads],
-                                                       Tw[(dq - w + 1) * kLightThreads], shx));
+                    f = __funnelshift_r(Tw[(w + 1) * st], Tw[(w + 2) * st], sh);
+                    rc = rev_groups32(
+                        ~__funnelshift_r(Tw[(dq - w) * st], Tw[(dq - w + 1) * st], shx));
                 }
-                Xf[w * kLightThreads] = f;
-                Xr[w * kLightThreads] = rc;
+                Xf[w * st] = f;
+                Xr[w * st] = rc;
             }
             // seed lookups
             SeedRec seeds[kLightMaxSeeds];
@@ -176,7 +173,7 @@ __global__ void __launch_bounds__(kLightThreads) k_align_light(LightArgs a) {
                 rec.flags = (uint8_t)(kSeedValid | (p0 ? kSeedPass0 : 0));
                 rec.offset = (uint16_t)o;
                 rec.pad = 0;
-                const uint64_t v = col32(Xf, o) & kmer_mask(s);
+                const uint64_t v = col32(Xf, o, st) & kmer_mask(s);
                 uint32_t cnt = 0;
                 lookup_seed(a.slots, a.T, a.positions, v, s, &rec, &cnt, a.status, &c_slots);
                 ++c_seeds;
@@ -259,10 +256,9 @@ __global__ void __launch_bounds__(kLightThreads) k_align_light(LightArgs a) {
                             const uint64_t w0 = p >> 4;
                             const int tb = (int)(p & 15);
                             const int nwt = (tb + n_t + 15) / 16 + 2;
-                            for (int w = 0; w < nwt; ++w)
-                                Tw[w * kLightThreads] = __ldg(a.genome + w0 + w);
+                            for (int w = 0; w < nwt; ++w) Tw[w * st] = __ldg(a.genome + w0 + w);
                             c_words += nwt;
-                            d = lv_thread((key & 1) ? Xr : Xf, m, Tw, tb, n_t, L, R);
+                            d = lv_thread((key & 1) ? Xr : Xf, m, Tw, tb, n_t, L, R, st);
                         }
                         ++c_ed;
                         c_over += (d < 0);
@@ -337,11 +333,17 @@ __global__ void __launch_bounds__(kLightThreads) k_align_light(LightArgs a) {
 
 }  // namespace
 
+// Shared-memory limit of the thread-per-read kernel, set once (before any capture).
+int light_prepare() {
+    return raise_smem_limit((const void*)k_align_light, (size_t)kLightWords * 256 * 4);
+}
+
 // Launch the thread-per-read bucket over all n reads; reads it does not take
 // are appended to heavy_ids (count in *heavy_count, cleared here).
 int launch_light(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
                  const snap_params* p, snap_result* d_out, cudaStream_t stream,
-                 const BatchPrep& bp, uint32_t* heavy_ids, unsigned long long* heavy_count) {
+                 const BatchPrep& bp, uint32_t* heavy_ids, unsigned long long* heavy_count,
+                 int threads) {
     LightArgs a;
     memset(&a, 0, sizeof(a));
     a.genome = idx->genome_words;
@@ -366,13 +368,12 @@ int launch_light(const snap_index* idx, Engine* e, const uint64_t* d_offsets, ui
     BatchStats* d_st = static_cast<BatchStats*>(e->stats.p);
     a.status = &d_st->status;
     a.ctr = &d_st->ctr;
-    const size_t smem = (size_t)kLightWords * kLightThreads * 4;
-    static_assert((size_t)kLightWords * kLightThreads * 4 <= 48 * 1024,
-                  "light bucket fits the default shared-memory limit");
+    if (threads != 64 && threads != 128 && threads != 256) threads = 128;
+    const size_t smem = (size_t)kLightWords * threads * 4;
     SNAP_CUDA(cudaMemsetAsync(heavy_count, 0, sizeof(unsigned long long), stream), "clear");
-    const uint64_t blocks = (n + kLightThreads - 1) / kLightThreads;
+    const uint64_t blocks = (n + threads - 1) / threads;
     e->launches++;
-    k_align_light<<<(unsigned)blocks, kLightThreads, smem, stream>>>(a);
+    k_align_light<<<(unsigned)blocks, threads, smem, stream>>>(a);
     SNAP_CUDA(cudaGetLastError(), "light launch");
     return SNAP_OK;
 }

@@ -486,9 +486,7 @@ int align_plain(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uin
         set_error("snap_align_plain: reads too long for the distance stage");
         return SNAP_E_INVAL;
     }
-    SNAP_CUDA(cudaFuncSetAttribute(k_plain_distance, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem),
-              "smem attr");
+    if ((rc = raise_smem_limit((const void*)k_plain_distance, (size_t)(int)smem))) return rc;
     int per_sm = 1;
     SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plain_distance,
                                                             warps * 32, smem),

@@ -156,6 +156,40 @@ def test_hand_built_branch_cases(snap):
             assert_same(got, ref, f"branch cases {kw}")
 
 
+def test_autotune_and_graph_replay_keep_results(snap):
+    # launch shapes and graph replay must never change a result: compare against the
+    # untuned, ungraphed run on several batch sizes, through the graph update path
+    import torch
+    w = synth.CONFIGS["C2"].scaled(G=3_000_000, n_reads=30_000)
+    g, _ = w.make_genome()
+    rd = w.make_reads(g)
+    gi = snap.Index(g, w.seed_len)
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.Stream()
+    d_b = torch.from_numpy(rd.bases).to(dev)
+    d_o = torch.from_numpy(rd.offsets.view(np.int64)).to(dev)
+
+    def run(n):
+        out = torch.zeros((n, 16), dtype=torch.uint8, device=dev)
+        gi.align_device(d_b, d_o[:n + 1], out, stream=stream, **w.params())
+        stream.synchronize()
+        return out.cpu().numpy().view(snap.RESULT_DTYPE).reshape(-1), gi.last_call_stats()
+
+    gi.configure(autotune=False, cuda_graphs=False)
+    refs = {n: run(n)[0] for n in (30_000, 20_000, 9_000)}
+    gi.configure(autotune=True, cuda_graphs=True)
+    shapes = set()
+    for n in (30_000, 30_000, 20_000, 9_000, 30_000):
+        got, st = run(n)
+        assert_same(got, refs[n], f"tuned/graph n={n}")
+        assert st["graph_replay"] == 1
+        shapes.add((st["light_threads"], st["warps_per_block"], st["table_slots"]))
+    assert all(t in (64, 128, 256) for t, _, _ in shapes)
+    ref_oracle, _ = oracle.Index(g, w.seed_len).align(rd.bases, rd.offsets, threads=4,
+                                                      **w.params())
+    assert_same(refs[30_000], ref_oracle, "untuned vs oracle")
+
+
 def test_empty_batch_and_bad_input(snap):
     g, _ = synth.genome(100_000, 0.0)
     gi = snap.Index(g, 20)
