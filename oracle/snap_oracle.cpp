@@ -441,11 +441,41 @@ void* or_index_build(const uint8_t* genome_ascii, uint64_t G, int s, const uint6
     } else {
         idx->entries.reserve(npos);
     }
-    uint64_t v = kmer_value(idx->genome.data(), s);
-    for (uint64_t l = 0; l < npos; ++l) {
-        if (l > 0) v = ((v << 2) | idx->genome[l + s - 1]) & mask;
-        if (filter && !std::binary_search(filt.begin(), filt.end(), v)) continue;
-        idx->entries.emplace_back(v, (uint32_t)l);
+    if (!filter) {
+        uint64_t v = kmer_value(idx->genome.data(), s);
+        for (uint64_t l = 0; l < npos; ++l) {
+            if (l > 0) v = ((v << 2) | idx->genome[l + s - 1]) & mask;
+            idx->entries.emplace_back(v, (uint32_t)l);
+        }
+    } else {
+        // Restricted build: a bitmap of hashed filter keys screens each window
+        // before the exact binary search, and position ranges are scanned by
+        // several threads; the kept entries are exactly those of the full build
+        // whose s-mer is in the filter.
+        const int hb = 27;
+        std::vector<uint64_t> bits((1ull << hb) / 64, 0);
+        auto h = [&](uint64_t k) { return (k * 0x9E3779B97F4A7C15ull) >> (64 - hb); };
+        for (uint64_t k : filt) bits[h(k) >> 6] |= 1ull << (h(k) & 63);
+        int nt = (int)std::thread::hardware_concurrency();
+        if (nt < 1) nt = 1;
+        if (nt > 64) nt = 64;
+        std::vector<std::vector<std::pair<uint64_t, uint32_t>>> part(nt);
+        auto scan = [&](int t) {
+            const uint64_t l0 = npos * t / nt, l1 = npos * (t + 1) / nt;
+            if (l0 >= l1) return;
+            uint64_t v = kmer_value(idx->genome.data() + l0, s);
+            for (uint64_t l = l0; l < l1; ++l) {
+                if (l > l0) v = ((v << 2) | idx->genome[l + s - 1]) & mask;
+                const uint64_t hv = h(v);
+                if (!(bits[hv >> 6] >> (hv & 63) & 1)) continue;
+                if (std::binary_search(filt.begin(), filt.end(), v))
+                    part[t].emplace_back(v, (uint32_t)l);
+            }
+        };
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t) th.emplace_back(scan, t);
+        for (auto& x : th) x.join();
+        for (auto& pv : part) idx->entries.insert(idx->entries.end(), pv.begin(), pv.end());
     }
     std::sort(idx->entries.begin(), idx->entries.end());
     return idx;
