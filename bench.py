@@ -50,6 +50,13 @@ def _args():
     ap.add_argument("--workload", default="C2")
     ap.add_argument("--form", choices=["batched", "plain"], default="batched")
     ap.add_argument("--reads", type=int, default=0, help="override reads per step")
+    ap.add_argument("--batch", type=int, default=4_000_000,
+                    help="reads per align call; a step aligns all the workload's reads")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving run (C4 recipe): Poisson arrivals at --load x the measured "
+                         "capacity, p50/p99 request latency")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--load", type=float, default=0.7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -175,7 +182,16 @@ def cpu_oracle_sample(w, g, rd, dpr, target_s: float = 12.0, max_reads: int = 40
     """Time the oracle (as it stands) on a bounded sample on all host cores."""
     import oracle
     cores = os.cpu_count() or 1
-    idx = oracle.Index(g, w.seed_len)
+    restricted = w.G > 500_000_000
+    if restricted:
+        # a full sorted index of a 3.1 Gbp genome takes minutes and ~50 GB; the
+        # oracle then indexes only the seeds of the sampled reads (same results)
+        max_reads = min(max_reads, 100_000)
+        cand = rd.subset(np.arange(min(rd.n, max_reads)))
+        idx = oracle.Index(g, w.seed_len, kmer_filter=oracle.read_seed_kmers(
+            cand.bases, cand.offsets, w.seed_len, w.num_seeds))
+    else:
+        idx = oracle.Index(g, w.seed_len)
     probe = rd.subset(np.arange(min(rd.n, 20_000)))
     pd = None if dpr is None else dpr[:probe.n]
     t0 = time.perf_counter()
@@ -189,8 +205,10 @@ def cpu_oracle_sample(w, g, rd, dpr, target_s: float = 12.0, max_reads: int = 40
     res, _ = idx.align(sub.bases, sub.offsets, max_dist_per_read=sd, threads=cores,
                        **w.params())
     dt = time.perf_counter() - t0
+    what = ("index restricted to the sampled reads' seeds" if restricted
+            else "index over the full genome")
     return dict(value=n / dt, unit="reads/s", cores=cores, kind="oracle",
-                sample=f"first {n} reads of the workload, index over the full genome "
+                sample=f"first {n} reads of the workload, {what} "
                        f"(built in {idx.build_seconds:.1f} s, not timed)"), sample, res
 
 
@@ -267,9 +285,18 @@ def run_ours(args):
     # replay its launch sequence as a CUDA graph
     stream = torch.cuda.Stream(device=dev)
 
+    batch = max(1, min(args.batch, n))
+
     def one_step(form_plain):
-        idx.align_device(d_b, d_o, d_out, d_max_dist_per_read=d_dpr, stream=stream,
-                         plain=form_plain, **params)
+        # all the workload's reads, `batch` reads per call; returns each call's stats
+        calls = []
+        for b0 in range(0, n, batch):
+            nb = min(batch, n - b0)
+            idx.align_device(d_b, d_o[b0:b0 + nb + 1], d_out[b0:b0 + nb],
+                             d_max_dist_per_read=None if d_dpr is None else d_dpr[b0:b0 + nb],
+                             stream=stream, plain=form_plain, **params)
+            calls.append(idx.last_call_stats())
+        return calls
 
     def timed(form_plain, steps, warmup):
         for _ in range(warmup):
@@ -287,9 +314,14 @@ def run_ours(args):
             for k in range(steps):
                 flush.zero_()  # L2 flush outside the event pair
                 evs[k][0].record(stream)
-                one_step(form_plain)
+                calls = one_step(form_plain)
                 evs[k][1].record(stream)
-                stats.append(idx.last_call_stats())
+                agg = dict(calls[-1])
+                for key in ("kernel_launches", "align_ms", "reads", "read_bases", "seeds",
+                            "slot_reads", "list_entries", "ed_calls", "ed_over",
+                            "window_bytes"):
+                    agg[key] = sum(c[key] for c in calls)
+                stats.append(agg)
             torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
@@ -331,7 +363,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": w.name, "genome_bp": w.G, "repeat_frac": w.repeat_frac,
-                   "reads_per_step": n, "read_len": "100" if w.len_mode == 0 else "mixed",
+                   "reads_per_step": n, "reads_per_call": batch,
+                   "read_len": "100" if w.len_mode == 0 else "mixed",
                    "seed_len": w.seed_len, **params, "form": args.form,
                    "l2": "flushed between steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single"},
@@ -366,12 +399,19 @@ def run_ours(args):
         pin_out = torch.zeros((n, 16), dtype=torch.uint8).pin_memory()
         nb, no = pin_b.numpy(), pin_o.numpy().view(np.uint64)
         no_out = pin_out.numpy().view(snap.RESULT_DTYPE).reshape(-1)
+        def e2e_step():
+            for b0 in range(0, n, batch):
+                m_ = min(batch, n - b0)
+                idx.align(nb, no[b0:b0 + m_ + 1],
+                          max_dist_per_read=None if dpr is None else dpr[b0:b0 + m_],
+                          out=no_out[b0:b0 + m_], plain=plain, **params)
+
         for _ in range(2):
-            idx.align(nb, no, max_dist_per_read=dpr, out=no_out, plain=plain, **params)
+            e2e_step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            idx.align(nb, no, max_dist_per_read=dpr, out=no_out, plain=plain, **params)
+            e2e_step()
         e2e_s = time.perf_counter() - t0
         line["e2e"] = {"value": n * args.e2e_steps / e2e_s, "unit": "reads/s",
                        "h2d_bytes_per_step": int(rd.bases.nbytes + rd.offsets.nbytes +
@@ -392,10 +432,84 @@ def run_ours(args):
     return 0
 
 
+def run_serve(args):
+    """C4 serving run: requests of log-uniform size (1k-100k reads; 80% 100 bp, 20%
+    1-10 kb), first all submitted at once to measure capacity, then submitted at
+    Poisson arrival times at --load x capacity; latency = completion - arrival."""
+    import torch
+
+    import paper_1111_5572_gb300 as snap
+    import synth
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    w = synth.CONFIGS["C4"]
+    t0 = time.perf_counter()
+    g, _ = w.make_genome()
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gi = snap.Index(g, w.seed_len)
+    build_s = time.perf_counter() - t0
+    _, sizes = synth.arrivals(args.requests, 1.0, 1000, 100_000)
+    reqs, first = [], 0
+    for k, nr in enumerate(sizes.tolist()):
+        lens = synth.read_lengths(nr, 2, 100, 1000, 10000, 0.8, seed=1000 + k)
+        rd = synth.reads(g, lens, w.sub_rate, w.indel_rate, w.indel_len, first_index=first)
+        first += nr
+        reqs.append((rd, w.max_dist_per_read(rd.lengths())))
+    total_reads = int(sum(r.n for r, _ in reqs))
+    total_bases = int(sum(int(r.offsets[-1]) for r, _ in reqs))
+    srv = snap.Server(gi, mem_budget_bytes=64 << 30, max_inflight=4)
+    # warm-up (tuning, graphs) on the first requests
+    for rd, dpr in reqs[:3]:
+        srv.wait(srv.submit(rd.bases, rd.offsets, max_dist_per_read=dpr, **w.params()))
+    # capacity: everything submitted at once
+    t0 = time.perf_counter()
+    tk = [srv.submit(rd.bases, rd.offsets, max_dist_per_read=dpr, **w.params())
+          for rd, dpr in reqs]
+    for t in tk:
+        srv.wait(t)
+    cap_s = time.perf_counter() - t0
+    capacity = total_reads / cap_s
+    # open loop: Poisson arrivals at load x capacity (requests/s)
+    rate = args.load * capacity / (total_reads / len(reqs))
+    times, _ = synth.arrivals(args.requests, rate, 1000, 100_000)
+    lat = [0.0] * len(reqs)
+    tickets = [None] * len(reqs)
+    with ClockSampler(0) as clk:
+        start = time.perf_counter()
+        for k, (rd, dpr) in enumerate(reqs):
+            delay = start + float(times[k]) - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = srv.submit(rd.bases, rd.offsets, max_dist_per_read=dpr, **w.params())
+        for k in range(len(reqs)):
+            _, lat[k] = srv.wait(tickets[k])
+        wall = time.perf_counter() - start
+    srv.close()
+    line = {
+        "metric": METRIC, "mode": "serve", "value": total_reads / wall, "unit": "reads/s",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": w.name, "genome_bp": w.G, "requests": len(reqs),
+                   "reads": total_reads, "bases": total_bases, "max_inflight": 4,
+                   "offered_load": args.load, "arrival_rate_per_s": rate},
+        "capacity_reads_per_s": capacity, "capacity_bases_per_s": total_bases / cap_s,
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(max(lat))},
+        "bases_per_s": total_bases / wall, "index_build_s": build_s, "genome_gen_s": gen_s,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -133,36 +133,60 @@ __global__ void k_pack_reads(const uint8_t* __restrict__ reads, uint64_t base, u
 }
 
 // ---------------------------------------------------------------------------
-// per-read candidate table (shared or global memory through generic pointers)
+// per-read candidate table (shared or global memory through generic pointers).
+// The table is an open-addressing hash of (strand, p) keys sized for the read's
+// seed hits; a dense list holds the slots in use, so picks and the clean-up
+// after a read cost the number of distinct candidates, not the table size.
+// Tables are left empty after every read.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void table_add(CandSlot* tab, uint32_t mask, unsigned long long key,
-                                          int* status) {
+__device__ __forceinline__ CandSlot empty_slot() {
+    CandSlot e;
+    e.key = kEmptyKey;
+    e.votes = 0;
+    e.state = kUnscored;
+    return e;
+}
+
+// Adds one vote for key; returns the slot and whether the key is new.
+__device__ __forceinline__ uint32_t table_add(CandSlot* tab, uint32_t mask, unsigned long long key,
+                                              int* status, bool* inserted) {
     uint32_t h = (uint32_t)mix64(key) & mask;
     for (uint32_t step = 0; step <= mask; ++step) {
         const unsigned long long prev = atomicCAS(&tab[h].key, kEmptyKey, key);
         if (prev == kEmptyKey || prev == key) {
             atomicAdd(&tab[h].votes, 1u);
-            return;
+            *inserted = (prev == kEmptyKey);
+            return h;
         }
         h = (h + 1) & mask;
     }
     atomicOr(status, kStTableFull);
+    *inserted = false;
+    return 0;
 }
 
 // most-voted unscored candidate, ties to the smaller key; 0 = none.
 // packed = votes(11 bits) | (kKeyMask - key)(33 bits) | slot(20 bits)
-__device__ __forceinline__ unsigned long long table_pick(const CandSlot* tab, uint32_t cap,
-                                                         int lane) {
+__device__ __forceinline__ unsigned long long table_pick(const CandSlot* tab,
+                                                         const uint32_t* dense, int nd, int lane) {
     unsigned long long best = 0;
-    for (uint32_t j = lane; j < cap; j += 32) {
-        const CandSlot c = tab[j];
-        if (c.key != kEmptyKey && c.state == kUnscored) {
+    for (int j = lane; j < nd; j += 32) {
+        const uint32_t slot = dense[j];
+        const CandSlot c = tab[slot];
+        if (c.state == kUnscored) {
             const unsigned long long v = ((unsigned long long)c.votes << 53) |
-                                         ((kKeyMask - c.key) << 20) | (unsigned long long)j;
+                                         ((kKeyMask - c.key) << 20) | (unsigned long long)slot;
             best = v > best ? v : best;
         }
     }
     return warp_max_u64(best);
+}
+
+// Initialise per-warp global candidate tables once after they are allocated.
+__global__ void k_init_ctab(CandSlot* tab, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        tab[i] = empty_slot();
 }
 
 __device__ __forceinline__ unsigned long long bucket_of(unsigned long long key) {
@@ -188,8 +212,9 @@ struct FusedArgs {
     uint8_t shifts[32];
     int n_shifts;
     snap_result* out;
-    CandSlot* gtab;  // per-warp overflow tables, gcap slots each
-    HitRec* ghits;   // per-warp overflow hit lists, gcap / 2 each
+    CandSlot* gtab;   // per-warp overflow tables, gcap slots each (kept empty)
+    HitRec* ghits;    // per-warp overflow hit lists, gcap / 2 each
+    uint32_t* gdense; // per-warp dense slot lists, gcap / 2 each
     uint32_t gcap;
     int* status;
     DevCounters* ctr;
@@ -197,7 +222,7 @@ struct FusedArgs {
     // multiple of 4 words (16 bytes) because SeedRec / CandSlot / HitRec are
     // moved with 16-byte vector accesses
     int wx, wt, seed_cap, scap, lv_ints, warp_words;
-    int off_xr, off_tw, off_seeds, off_tab, off_hits, off_lv;
+    int off_xr, off_tw, off_seeds, off_tab, off_hits, off_dense, off_lv;
 };
 
 struct WarpCounters {
@@ -228,10 +253,12 @@ struct WarpMem {
     SeedRec* seeds;
     CandSlot* stab;
     HitRec* shits;
+    uint32_t* sdense;
     int* lvA;
     int* lvB;
     CandSlot* gtab;
     HitRec* ghits;
+    uint32_t* gdense;
 };
 
 // Edit distance of candidate `key` at limit L (warp-wide, result uniform).  LVD
@@ -326,28 +353,25 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
         while (cap < 2u * H) cap <<= 1;
         CandSlot* tab;
         HitRec* hits;
+        uint32_t* dense;
         bool ok = true;
         if (cap <= (uint32_t)a.scap) {
             tab = wm.stab;
             hits = wm.shits;
+            dense = wm.sdense;
         } else if (wm.gtab && cap <= a.gcap) {
             tab = wm.gtab;
             hits = wm.ghits;
+            dense = wm.gdense;
         } else {
             tab = nullptr;
             hits = nullptr;
+            dense = nullptr;
             ok = false;
             if (lane == 0) atomicOr(a.status, kStTableFull);
         }
         if (ok) {
-            for (uint32_t j = lane; j < cap; j += 32) {
-                CandSlot e;
-                e.key = kEmptyKey;
-                e.votes = 0;
-                e.state = kUnscored;
-                tab[j] = e;
-            }
-            __syncwarp();
+            int nd = 0;  // distinct candidates so far (slots listed in dense)
             int d_best = kInf, d_second = kInf, nh = 0, t = 0;
             unsigned long long best_key = 0;
             bool any_nonpopular = false, returned = false;
@@ -405,27 +429,36 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                     any_nonpopular = true;
                 const int o = rec.offset;
                 const int tot = (int)rec.fwd_n + rec.rc_n;
-                for (int j = lane; j < tot; j += 32) {
-                    const bool fwd = j < rec.fwd_n;
-                    uint32_t l;
-                    if (fwd) {
-                        l = (rec.flags & kSeedFwdInline) ? rec.fwd_ref
-                                                         : __ldg(a.positions + rec.fwd_ref + j);
-                    } else {
-                        const int jj = j - rec.fwd_n;
-                        l = (rec.flags & kSeedRcInline) ? rec.rc_ref
-                                                        : __ldg(a.positions + rec.rc_ref + jj);
+                for (int j0 = 0; j0 < tot; j0 += 32) {
+                    const int j = j0 + lane;
+                    bool ins = false;
+                    uint32_t slot = 0;
+                    if (j < tot) {
+                        const bool fwd = j < rec.fwd_n;
+                        uint32_t l;
+                        if (fwd) {
+                            l = (rec.flags & kSeedFwdInline)
+                                    ? rec.fwd_ref : __ldg(a.positions + rec.fwd_ref + j);
+                        } else {
+                            const int jj = j - rec.fwd_n;
+                            l = (rec.flags & kSeedRcInline)
+                                    ? rec.rc_ref : __ldg(a.positions + rec.rc_ref + jj);
+                        }
+                        wc.list_entries += (rec.flags & kSeedFwdInline) ? 0u : 1u;
+                        const long long p = fwd ? (long long)l - o : (long long)l - (m - o - s);
+                        if (p >= 0)
+                            slot = table_add(tab, cap - 1,
+                                             2ull * (unsigned long long)p + (fwd ? 0 : 1),
+                                             a.status, &ins);
                     }
-                    wc.list_entries += (rec.flags & kSeedFwdInline) ? 0u : 1u;
-                    const long long p = fwd ? (long long)l - o : (long long)l - (m - o - s);
-                    if (p >= 0)
-                        table_add(tab, cap - 1, 2ull * (unsigned long long)p + (fwd ? 0 : 1),
-                                  a.status);
+                    const unsigned nb = __ballot_sync(kFull, ins);
+                    if (ins) dense[nd + __popc(nb & ((1u << lane) - 1))] = slot;
+                    nd += __popc(nb);
                 }
                 __syncwarp();
                 if (rec.flags & kSeedPass0) ++t;
                 }
-                const unsigned long long pk = table_pick(tab, cap, lane);
+                const unsigned long long pk = table_pick(tab, dense, nd, lane);
                 if (pk) {
                     score(pk);
                 } else if (draining) {
@@ -452,6 +485,10 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                 res_strand = (int)(best_key & 1);
                 res_d = d_best;
             }
+            // leave the table empty for the next read
+            __syncwarp();
+            for (int j = lane; j < nd; j += 32) tab[dense[j]] = empty_slot();
+            __syncwarp();
         }
     }
     if (lane == 0) {
@@ -476,11 +513,15 @@ __global__ void __launch_bounds__(256, 4) k_align_fused(FusedArgs a) {
     wm.seeds = reinterpret_cast<SeedRec*>(base + a.off_seeds);
     wm.stab = reinterpret_cast<CandSlot*>(base + a.off_tab);
     wm.shits = reinterpret_cast<HitRec*>(base + a.off_hits);
+    wm.sdense = base + a.off_dense;
     wm.lvA = a.lv_ints ? reinterpret_cast<int*>(base + a.off_lv) : nullptr;
     wm.lvB = a.lv_ints ? wm.lvA + a.lv_ints / 2 : nullptr;
     const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     wm.gtab = a.gtab ? a.gtab + gw * a.gcap : nullptr;
     wm.ghits = a.ghits ? a.ghits + gw * (a.gcap / 2) : nullptr;
+    wm.gdense = a.gdense ? a.gdense + gw * (a.gcap / 2) : nullptr;
+    for (int j = lane; j < a.scap; j += 32) wm.stab[j] = empty_slot();
+    __syncwarp();
     WarpCounters wc;
     const unsigned long long n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
     for (;;) {
@@ -565,10 +606,11 @@ Engine* engine_create() {
 
 void engine_destroy(Engine* e) {
     if (!e) return;
-    for (DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->heavy,
-                      &e->h_reads, &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds, &e->p_hits,
+    for (DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->gdense,
+                      &e->heavy, &e->h_reads, &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds,
+                      &e->p_hits,
                       &e->p_hitoff, &e->p_partial, &e->p_table, &e->p_events, &e->p_hitlist,
-                      &e->p_items, &e->p_misc})
+                      &e->p_items, &e->p_misc, &e->p_dense})
         b->release();
     e->pin.release();
     for (auto& ev : e->ev)
@@ -584,10 +626,11 @@ void engine_destroy(Engine* e) {
 
 size_t engine_bytes(const Engine* e) {
     size_t s = 0;
-    for (const DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->heavy,
+    for (const DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->gdense,
+                            &e->heavy,
                             &e->h_reads, &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds,
                             &e->p_hits, &e->p_hitoff, &e->p_partial, &e->p_table, &e->p_events,
-                            &e->p_hitlist, &e->p_items, &e->p_misc})
+                            &e->p_hitlist, &e->p_items, &e->p_misc, &e->p_dense})
         s += b->bytes;
     return s;
 }
@@ -597,9 +640,11 @@ void engine_release(Engine* e) {
         cudaGraphExecDestroy(e->gexec);  // it points into the workspaces
         e->gexec = nullptr;
     }
-    for (DevBuf* b : {&e->packed, &e->gtab, &e->ghits, &e->heavy, &e->h_reads, &e->h_offsets,
+    e->gtab_ready = false;
+    for (DevBuf* b : {&e->packed, &e->gtab, &e->ghits, &e->gdense, &e->heavy, &e->h_reads,
+                      &e->h_offsets,
                       &e->h_out, &e->h_dmax, &e->p_seeds, &e->p_hits, &e->p_hitoff, &e->p_partial,
-                      &e->p_table, &e->p_events, &e->p_hitlist, &e->p_items, &e->p_misc})
+                      &e->p_table, &e->p_events, &e->p_hitlist, &e->p_items, &e->p_misc, &e->p_dense})
         b->release();
 }
 
@@ -808,11 +853,11 @@ static int plan_fused(const snap_index* idx, Engine* e, const uint64_t* d_offset
     // the shared candidate table holds reads with up to scap/2 seed hits; reads
     // with more use the warp's global table
     const int fixed_words = 2 * a.wx + a.wt + 4 * a.seed_cap + a.lv_ints;
-    const int budget_words = 200 * 1024 / 4;  // per block
+    const int budget_words = 200 * 1024 / 4;  // per block; 6.5 words per table slot
     int warps = std::max(1, shape.warps);
-    while (warps > 1 && warps * (fixed_words + 6 * 64) > budget_words) warps >>= 1;
+    while (warps > 1 && warps * (fixed_words + 7 * 64) > budget_words) warps >>= 1;
     int scap = std::max(64, shape.scap);
-    while (scap > 64 && warps * (fixed_words + 6 * scap) > budget_words) scap >>= 1;
+    while (scap > 64 && warps * (fixed_words + 7 * scap) > budget_words) scap >>= 1;
     shape.warps = warps;
     shape.scap = scap;
     a.scap = scap;
@@ -821,9 +866,10 @@ static int plan_fused(const snap_index* idx, Engine* e, const uint64_t* d_offset
     a.off_seeds = a.off_tw + a.wt;
     a.off_tab = a.off_seeds + 4 * a.seed_cap;     // SeedRec: 4 words
     a.off_hits = a.off_tab + 4 * scap;            // CandSlot: 4 words
-    a.off_lv = a.off_hits + 4 * (scap / 2);       // HitRec: 4 words, scap/2 of them
+    a.off_dense = a.off_hits + 4 * (scap / 2);    // HitRec: 4 words, scap/2 of them
+    a.off_lv = a.off_dense + up4(scap / 2);       // dense slot list: scap/2 words
     a.warp_words = a.off_lv + a.lv_ints;
-    if ((a.off_seeds | a.off_tab | a.off_hits | a.off_lv | a.warp_words) & 3) {
+    if ((a.off_seeds | a.off_tab | a.off_hits | a.off_dense | a.off_lv | a.warp_words) & 3) {
         set_error("snap_align: internal shared-memory layout is not 16-byte aligned");
         return SNAP_E_INTERNAL;
     }
@@ -855,14 +901,29 @@ static int plan_fused(const snap_index* idx, Engine* e, const uint64_t* d_offset
         return SNAP_E_INVAL;
     }
     if (gcap > (uint64_t)scap) {
-        const uint64_t per_warp = gcap * (sizeof(CandSlot) + sizeof(HitRec) / 2);
+        const uint64_t per_warp = gcap * (sizeof(CandSlot) + sizeof(HitRec) / 2 + 2);
         const uint64_t max_warps = std::max<uint64_t>(1, e->overflow_budget / per_warp);
         if (blocks * warps > max_warps) blocks = std::max<uint64_t>(1, max_warps / warps);
         const uint64_t tw = blocks * warps;
-        if ((rc = e->gtab.ensure(tw * gcap * sizeof(CandSlot), "overflow tables"))) return rc;
+        const uint64_t tslots = tw * gcap;
+        void* before = e->gtab.p;
+        const size_t before_bytes = e->gtab.bytes;
+        if ((rc = e->gtab.ensure(tslots * sizeof(CandSlot), "overflow tables"))) return rc;
         if ((rc = e->ghits.ensure(tw * (gcap / 2) * sizeof(HitRec), "overflow hits"))) return rc;
+        if ((rc = e->gdense.ensure(tw * (gcap / 2) * sizeof(uint32_t), "overflow lists")))
+            return rc;
+        if (e->gtab.p != before || e->gtab.bytes != before_bytes || !e->gtab_ready) {
+            // fresh tables start empty; kernels keep them empty afterwards
+            const uint64_t all = e->gtab.bytes / sizeof(CandSlot);
+            k_init_ctab<<<grid_cap(e->sms, all, 256), 256>>>(static_cast<CandSlot*>(e->gtab.p),
+                                                            all);
+            SNAP_CUDA(cudaGetLastError(), "table init");
+            SNAP_CUDA(cudaDeviceSynchronize(), "table init");
+            e->gtab_ready = true;
+        }
         a.gtab = static_cast<CandSlot*>(e->gtab.p);
         a.ghits = static_cast<HitRec*>(e->ghits.p);
+        a.gdense = static_cast<uint32_t*>(e->gdense.p);
         a.gcap = (uint32_t)gcap;
     }
     if ((rc = e->head.ensure(64, "queue head"))) return rc;
@@ -1283,16 +1344,17 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
     const int fixed_words = 2 * a.wx + a.wt + 4 * a.seed_cap + a.lv_ints;
     int warps = 8;
     const int budget_words = 200 * 1024 / 4;
-    while (warps > 1 && warps * (fixed_words + 6 * 64) > budget_words) warps >>= 1;
+    while (warps > 1 && warps * (fixed_words + 7 * 64) > budget_words) warps >>= 1;
     int scap = 1024;
-    while (scap > 64 && warps * (fixed_words + 6 * scap) > budget_words) scap >>= 1;
+    while (scap > 64 && warps * (fixed_words + 7 * scap) > budget_words) scap >>= 1;
     a.scap = scap;
     a.off_xr = a.wx;
     a.off_tw = 2 * a.wx;
     a.off_seeds = a.off_tw + a.wt;
     a.off_tab = a.off_seeds + 4 * a.seed_cap;
     a.off_hits = a.off_tab + 4 * scap;
-    a.off_lv = a.off_hits + 4 * (scap / 2);
+    a.off_dense = a.off_hits + 4 * (scap / 2);
+    a.off_lv = a.off_dense + up4(scap / 2);
     a.warp_words = a.off_lv + a.lv_ints;
     const size_t smem = (size_t)warps * a.warp_words * 4;
     if (smem > 227 * 1024) {
@@ -1317,7 +1379,7 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
     }
     if (gcap > (uint64_t)scap) {
         // per-warp tables in the array; fewer warps when they would not fit
-        const uint64_t per_warp = gcap * (sizeof(CandSlot) + sizeof(HitRec) / 2);
+        const uint64_t per_warp = gcap * (sizeof(CandSlot) + sizeof(HitRec) / 2 + 2);
         const uint64_t max_warps = kNoAllocTableBytes / per_warp;
         if (max_warps < 1) {
             set_error("%s: seeds x max_hits per read (%llu) needs %llu bytes of candidate "
@@ -1335,9 +1397,15 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
             }
             blocks = std::max<uint64_t>(1, max_warps / warps);
         }
+        const uint64_t tw = blocks * warps;
         a.gtab = reinterpret_cast<CandSlot*>(d_tables);
-        a.ghits = reinterpret_cast<HitRec*>(d_tables + blocks * warps * gcap * sizeof(CandSlot));
+        a.ghits = reinterpret_cast<HitRec*>(d_tables + tw * gcap * sizeof(CandSlot));
+        a.gdense = reinterpret_cast<uint32_t*>(d_tables + tw * gcap * sizeof(CandSlot) +
+                                               tw * (gcap / 2) * sizeof(HitRec));
         a.gcap = (uint32_t)gcap;
+        // the array keeps the previous call's contents: empty the tables this call uses
+        k_init_ctab<<<grid_cap(sms, tw * gcap, 256), 256, 0, stream>>>(a.gtab, tw * gcap);
+        SNAP_CUDA(cudaGetLastError(), "table init");
     }
     kfn<<<(unsigned)blocks, warps * 32, (size_t)warps * a.warp_words * 4, stream>>>(a);
     SNAP_CUDA(cudaGetLastError(), "align launch");

@@ -31,7 +31,8 @@ struct Engine {
     std::mutex mu;
     cudaStream_t own_stream = nullptr;
     int sms = 0;
-    DevBuf stats, head, packed, gtab, ghits, heavy;
+    DevBuf stats, head, packed, gtab, ghits, gdense, heavy;
+    bool gtab_ready = false;  // gtab holds only empty slots
     DevBuf h_reads, h_offsets, h_out, h_dmax;  // device copies for the host-buffer entry points
     PinnedBuf pin;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -48,7 +49,8 @@ struct Engine {
     int last_graph = 0;
     uint64_t overflow_budget = 4ull << 30;  // device bytes for per-warp global candidate tables
     // plain-form workspace
-    DevBuf p_seeds, p_hits, p_hitoff, p_partial, p_table, p_events, p_hitlist, p_items, p_misc;
+    DevBuf p_seeds, p_hits, p_hitoff, p_partial, p_table, p_events, p_hitlist, p_items, p_misc,
+        p_dense;
 };
 
 // Shared by both forms: batch statistics (one small device-to-host copy and

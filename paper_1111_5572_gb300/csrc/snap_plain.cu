@@ -55,6 +55,8 @@ struct PlainArgs {
     HitRec* hitlist;          // per read: hits entries at hit_off[r]
     unsigned long long* items;    // (read << 32) | slot
     unsigned long long* n_items;
+    uint32_t* dense;          // per read: the used table slots, at hit_off[r]
+    uint32_t* ndense;         // [n] number of used slots
     snap_result* out;
     int* status;
     DevCounters* ctr;
@@ -181,7 +183,8 @@ __global__ void k_plain_candidates(PlainArgs a) {
             cur += tot;
         }
         __syncwarp();
-        // one distance work item per distinct candidate
+        // one distance work item per distinct candidate, and the read's dense list
+        uint32_t nd = 0;
         for (uint32_t j0 = 0; j0 < cap; j0 += 32) {
             const uint32_t j = j0 + lane;
             const bool used = j < cap && tab[j].key != kEmptyKey;
@@ -192,8 +195,11 @@ __global__ void k_plain_candidates(PlainArgs a) {
             if (used) {
                 const unsigned rank = __popc(bal & ((1u << lane) - 1));
                 a.items[at + rank] = (r << 32) | j;
+                a.dense[base + nd + rank] = j;
             }
+            nd += __popc(bal);
         }
+        if (lane == 0) a.ndense[r] = nd;
     }
     add_counter(&a.ctr->list_entries, my_list);
 }
@@ -291,9 +297,12 @@ __global__ void k_plain_replay(PlainArgs a) {
                 if (d_second >= d_best + c) return d_best + c - 1;
                 return d_best - 1;
             };
+            const uint32_t nd = H ? a.ndense[r] : 0;
+            const uint32_t* dense = a.dense + base;
             auto pick = [&]() -> unsigned long long {
                 unsigned long long best = 0;
-                for (uint32_t j = lane; j < cap; j += 32) {
+                for (uint32_t q = lane; q < nd; q += 32) {
+                    const uint32_t j = dense[q];
                     const CandSlot e = tab[j];
                     // the table holds every seed's keys from the start; a key takes part
                     // only once a seed processed so far has voted for it
@@ -462,6 +471,10 @@ int align_plain(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uin
     if ((rc = e->p_events.ensure(Htot * sizeof(uint32_t), "hit events"))) return rc;
     if ((rc = e->p_hitlist.ensure(Htot * sizeof(HitRec), "hit lists"))) return rc;
     if ((rc = e->p_items.ensure(Htot * sizeof(unsigned long long), "work items"))) return rc;
+    if ((rc = e->p_dense.ensure(Htot * sizeof(uint32_t) + n * sizeof(uint32_t), "dense lists")))
+        return rc;
+    a.dense = static_cast<uint32_t*>(e->p_dense.p);
+    a.ndense = a.dense + Htot;
     a.table = static_cast<CandSlot*>(e->p_table.p);
     a.events = static_cast<uint32_t*>(e->p_events.p);
     a.hitlist = static_cast<HitRec*>(e->p_hitlist.p);
