@@ -43,6 +43,9 @@ __global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, i
     unsigned int my_len = 0;
     int my_L0 = 0, my_n = 0, bad = 0;
     unsigned long long my_hits = 0, my_light = 0;
+    unsigned long long c_n[kClasses] = {0, 0, 0, 0}, c_hits[kClasses] = {0, 0, 0, 0};
+    unsigned int c_len[kClasses] = {0, 0, 0, 0};
+    int c_L0[kClasses] = {0, 0, 0, 0}, c_seeds[kClasses] = {0, 0, 0, 0};
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
          r += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t a = offsets[r], b = offsets[r + 1];
@@ -67,6 +70,17 @@ __global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, i
         my_L0 = max(my_L0, dm + c - 1);
         my_light += (m <= (uint64_t)kLightBucketMaxM && nn <= kLightBucketMaxSeeds &&
                      dm + c - 1 <= kLightBucketMaxL);
+        const int k = length_class(m);
+#pragma unroll
+        for (int q = 0; q < kClasses; ++q) {
+            if (q != k) continue;
+            c_n[q] += 1;
+            c_len[q] = max(c_len[q], (unsigned int)m);
+            c_L0[q] = max(c_L0[q], dm + c - 1);
+            c_seeds[q] = max(c_seeds[q], nn);
+            const unsigned long long hh = (unsigned long long)nn * (unsigned long long)h_max;
+            c_hits[q] = hh > c_hits[q] ? hh : c_hits[q];
+        }
         my_n = max(my_n, nn);
         my_hits = max(my_hits, (unsigned long long)nn * (unsigned long long)h_max);
     }
@@ -80,6 +94,15 @@ __global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, i
         const unsigned long long h = __shfl_xor_sync(kFull, my_hits, o);
         my_hits = h > my_hits ? h : my_hits;
         my_light += __shfl_xor_sync(kFull, my_light, o);
+#pragma unroll
+        for (int q = 0; q < kClasses; ++q) {
+            c_n[q] += __shfl_xor_sync(kFull, c_n[q], o);
+            c_len[q] = max(c_len[q], __shfl_xor_sync(kFull, c_len[q], o));
+            c_L0[q] = max(c_L0[q], __shfl_xor_sync(kFull, c_L0[q], o));
+            c_seeds[q] = max(c_seeds[q], __shfl_xor_sync(kFull, c_seeds[q], o));
+            const unsigned long long hh = __shfl_xor_sync(kFull, c_hits[q], o);
+            c_hits[q] = hh > c_hits[q] ? hh : c_hits[q];
+        }
     }
     if ((threadIdx.x & 31) == 0) {
         if (bad) atomicOr(&st->status, bad);
@@ -88,6 +111,15 @@ __global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, i
         atomicMax(&st->max_seeds, my_n);
         atomicMax(&st->max_hits_bound, my_hits);
         if (my_light) atomicAdd(&st->n_light, my_light);
+#pragma unroll
+        for (int q = 0; q < kClasses; ++q) {
+            if (!c_n[q]) continue;
+            atomicAdd(&st->cls_n[q], c_n[q]);
+            atomicMax(&st->cls_max_len[q], c_len[q]);
+            atomicMax(&st->cls_max_L0[q], c_L0[q]);
+            atomicMax(&st->cls_max_seeds[q], c_seeds[q]);
+            atomicMax(&st->cls_max_hits[q], c_hits[q]);
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->total_bases = offsets[n] - offsets[0];
@@ -129,6 +161,41 @@ __global__ void k_pack_reads(const uint8_t* __restrict__ reads, uint64_t base, u
         }
         words[w] = word;
         if (bad) atomicOr(status, kStBadBase);
+    }
+}
+
+// Distribute the reads the warp kernel must take (the short-read bucket's
+// leftovers, or all reads) into per-length-class lists (warp-aggregated atomics).
+struct ClassLists {
+    uint32_t* list;                     // class q at list + off[q]
+    unsigned long long off[kClasses];
+    unsigned long long* count;          // [kClasses]
+};
+
+__global__ void k_split_classes(const uint32_t* __restrict__ ids,
+                                const unsigned long long* __restrict__ n_ids_dev, uint64_t n_all,
+                                const uint64_t* __restrict__ offsets, ClassLists cl) {
+    const uint64_t n_in = ids ? *n_ids_dev : n_all;
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t iters = (n_in + stride - 1) / stride;
+    for (uint64_t it = 0; it < iters; ++it) {
+        const uint64_t i = it * stride + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+        int k = -1;
+        uint32_t r = 0;
+        if (i < n_in) {
+            r = ids ? ids[i] : (uint32_t)i;
+            k = length_class(offsets[r + 1] - offsets[r]);
+        }
+#pragma unroll
+        for (int q = 0; q < kClasses; ++q) {
+            const unsigned mask = __ballot_sync(kFull, k == q);
+            if (!mask) continue;
+            unsigned long long base = 0;
+            if (lane == __ffs(mask) - 1) base = atomicAdd(cl.count + q, (unsigned long long)__popc(mask));
+            base = __shfl_sync(kFull, base, __ffs(mask) - 1);
+            if (k == q) cl.list[cl.off[q] + base + __popc(mask & ((1u << lane) - 1))] = r;
+        }
     }
 }
 
@@ -216,6 +283,7 @@ struct FusedArgs {
     HitRec* ghits;    // per-warp overflow hit lists, gcap / 2 each
     uint32_t* gdense; // per-warp dense slot lists, gcap / 2 each
     uint32_t gcap;
+    SeedRec* gseeds;  // per-warp seed records (seed_cap each) when not in shared memory
     int* status;
     DevCounters* ctr;
     // per-warp shared-memory layout, in 32-bit words; every section offset is a
@@ -510,7 +578,8 @@ __global__ void __launch_bounds__(256, 4) k_align_fused(FusedArgs a) {
     wm.Xf = base;
     wm.Xr = base + a.off_xr;
     wm.Tw = base + a.off_tw;
-    wm.seeds = reinterpret_cast<SeedRec*>(base + a.off_seeds);
+    wm.seeds = a.gseeds ? a.gseeds + ((uint64_t)blockIdx.x * (blockDim.x >> 5) + wib) * a.seed_cap
+                        : reinterpret_cast<SeedRec*>(base + a.off_seeds);
     wm.stab = reinterpret_cast<CandSlot*>(base + a.off_tab);
     wm.shits = reinterpret_cast<HitRec*>(base + a.off_hits);
     wm.sdense = base + a.off_dense;
@@ -537,13 +606,11 @@ __global__ void __launch_bounds__(256, 4) k_align_fused(FusedArgs a) {
 
 using FusedKernel = void (*)(FusedArgs);
 
-// The kernel variant for a batch whose largest limit is Lmax: the fewest
-// register diagonals per lane that cover [-Lmax, Lmax], else shared memory.
+// The kernel variant for a batch whose largest limit is Lmax: one or two
+// register diagonals per lane when they cover [-Lmax, Lmax], else shared memory.
 static FusedKernel fused_kernel_for(int Lmax) {
     if (Lmax <= 15) return k_align_fused<1>;
     if (Lmax <= 31) return k_align_fused<2>;
-    if (Lmax <= 63) return k_align_fused<4>;
-    if (Lmax <= 127) return k_align_fused<8>;
     return k_align_fused<0>;
 }
 
@@ -606,6 +673,7 @@ Engine* engine_create() {
 
 void engine_destroy(Engine* e) {
     if (!e) return;
+    for (DevBuf& b : e->gseeds) b.release();
     for (DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->gdense,
                       &e->heavy, &e->h_reads, &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds,
                       &e->p_hits,
@@ -626,6 +694,7 @@ void engine_destroy(Engine* e) {
 
 size_t engine_bytes(const Engine* e) {
     size_t s = 0;
+    for (const DevBuf& b : e->gseeds) s += b.bytes;
     for (const DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->gdense,
                             &e->heavy,
                             &e->h_reads, &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds,
@@ -636,6 +705,7 @@ size_t engine_bytes(const Engine* e) {
 }
 
 void engine_release(Engine* e) {
+    for (DevBuf& b : e->gseeds) b.release();
     if (e->gexec) {
         cudaGraphExecDestroy(e->gexec);  // it points into the workspaces
         e->gexec = nullptr;
@@ -803,24 +873,31 @@ static int finish_status(Engine* e, cudaStream_t stream, const char* where, uint
     return SNAP_OK;
 }
 
-// One launch plan of the batched form for a given shape: the warp kernel's
-// layout and grid, and whether the thread-per-read bucket runs first.
-struct FusedPlan {
-    FusedArgs a;
-    FusedKernel kfn = nullptr;
-    size_t smem = 0;
-    uint64_t blocks = 0;
+// The launch plan of the batched form for one shape: whether the short-read
+// bucket runs, and one warp-kernel launch per non-empty read-length class, each
+// laid out for its class's longest read and largest limit.
+struct BatchPlan {
     LaunchShape shape;
     bool light = false;
+    bool use[kClasses] = {false, false, false, false};
+    FusedArgs a[kClasses];
+    FusedKernel kfn[kClasses] = {nullptr, nullptr, nullptr, nullptr};
+    size_t smem[kClasses] = {0, 0, 0, 0};
+    uint64_t blocks[kClasses] = {0, 0, 0, 0};
+    int warps[kClasses] = {0, 0, 0, 0};
+    ClassLists cl;
+    uint32_t* heavy_ids = nullptr;
+    unsigned long long* head = nullptr;  // [0..3] class queue heads, [4] leftovers, [5..8] class counts
+    uint64_t table_slots[kClasses] = {0, 0, 0, 0};  // global candidate slots each class needs
 };
 
-// Lay out the warp kernel for `shape` and make sure every buffer exists (no
-// allocation happens after this, so the enqueue below can be captured).
-static int plan_fused(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
+// Lay out the warp kernel of class q; allocate what it needs (no allocation
+// happens after planning, so the enqueue can be captured).
+static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
                       const snap_params* p, snap_result* d_out, const BatchPrep& bp,
-                      LaunchShape shape, FusedPlan* plan) {
+                      const LaunchShape& shape, int q, BatchPlan* plan) {
     int rc;
-    FusedArgs& a = plan->a;
+    FusedArgs& a = plan->a[q];
     memset(&a, 0, sizeof(a));
     a.genome = idx->genome_words;
     a.G = idx->G;
@@ -831,8 +908,10 @@ static int plan_fused(const snap_index* idx, Engine* e, const uint64_t* d_offset
     a.rwords = bp.rwords;
     a.offsets = d_offsets;
     a.base0 = bp.base0;
-    a.order = nullptr;
+    a.order = plan->cl.list + plan->cl.off[q];
     a.n_items = n;
+    a.n_items_dev = plan->cl.count + q;
+    a.head = plan->head + q;
     a.d_max = p->max_dist;
     a.h_max = p->max_hits;
     a.c = p->conf_diff;
@@ -842,29 +921,30 @@ static int plan_fused(const snap_index* idx, Engine* e, const uint64_t* d_offset
     a.out = d_out;
     a.status = &static_cast<BatchStats*>(e->stats.p)->status;
     a.ctr = &static_cast<BatchStats*>(e->stats.p)->ctr;
-    const int mmax = std::max(1u, bp.st.max_len);
-    const int Lmax = std::max(0, bp.st.max_L0);
-    const int nmax = std::max(1, bp.st.max_seeds);
+    const int mmax = std::max(1u, bp.st.cls_max_len[q]);
+    const int Lmax = std::max(0, bp.st.cls_max_L0[q]);
+    const int nmax = std::max(1, bp.st.cls_max_seeds[q]);
     auto up4 = [](int w) { return (w + 3) & ~3; };
     a.wx = up4((mmax + 15) / 16 + 4);
     a.wt = up4((mmax + Lmax + 15 + 15) / 16 + 4);
     a.seed_cap = nmax;
-    a.lv_ints = Lmax > 127 ? up4(2 * (2 * Lmax + 4)) : 0;
-    // the shared candidate table holds reads with up to scap/2 seed hits; reads
-    // with more use the warp's global table
-    const int fixed_words = 2 * a.wx + a.wt + 4 * a.seed_cap + a.lv_ints;
-    const int budget_words = 200 * 1024 / 4;  // per block; 6.5 words per table slot
+    a.lv_ints = Lmax > 31 ? up4(2 * (2 * Lmax + 4)) : 0;
+    // many seeds (long reads): seed records in global memory, more warps per SM
+    const bool seeds_global = nmax > 64;
+    const int seed_words = seeds_global ? 0 : 4 * a.seed_cap;
+    const int fixed_words = 2 * a.wx + a.wt + seed_words + a.lv_ints;
+    const int budget_words = 200 * 1024 / 4;  // per block; 7 words per table slot
     int warps = std::max(1, shape.warps);
+    // a class with few reads spreads them over all SMs (one warp per read)
+    while (warps > 1 && bp.st.cls_n[q] < (uint64_t)e->sms * warps) warps >>= 1;
     while (warps > 1 && warps * (fixed_words + 7 * 64) > budget_words) warps >>= 1;
     int scap = std::max(64, shape.scap);
     while (scap > 64 && warps * (fixed_words + 7 * scap) > budget_words) scap >>= 1;
-    shape.warps = warps;
-    shape.scap = scap;
     a.scap = scap;
     a.off_xr = a.wx;
     a.off_tw = 2 * a.wx;
     a.off_seeds = a.off_tw + a.wt;
-    a.off_tab = a.off_seeds + 4 * a.seed_cap;     // SeedRec: 4 words
+    a.off_tab = a.off_seeds + seed_words;         // SeedRec: 4 words
     a.off_hits = a.off_tab + 4 * scap;            // CandSlot: 4 words
     a.off_dense = a.off_hits + 4 * (scap / 2);    // HitRec: 4 words, scap/2 of them
     a.off_lv = a.off_dense + up4(scap / 2);       // dense slot list: scap/2 words
@@ -880,19 +960,16 @@ static int plan_fused(const snap_index* idx, Engine* e, const uint64_t* d_offset
         return SNAP_E_INVAL;
     }
     const FusedKernel kfn = fused_kernel_for(Lmax);
-    if ((rc = raise_smem_limit((const void*)kfn, (size_t)(int)smem))) return rc;
+    if ((rc = raise_smem_limit((const void*)kfn, smem))) return rc;
     int per_sm = 0;
     SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem),
               "occupancy");
     if (per_sm < 1) per_sm = 1;
-    plan->light = bp.st.n_light > 0 && shape.light_threads > 0;
     uint64_t blocks = (uint64_t)e->sms * per_sm;
-    if (!plan->light) {
-        const uint64_t need_blocks = (n + warps - 1) / warps;
-        if (blocks > need_blocks) blocks = need_blocks;
-    }
+    const uint64_t need_blocks = (bp.st.cls_n[q] + warps - 1) / warps;
+    if (blocks > need_blocks) blocks = std::max<uint64_t>(1, need_blocks);
     // global overflow tables for reads whose candidate table outgrows shared memory
-    const uint64_t hb = bp.st.max_hits_bound;
+    const uint64_t hb = bp.st.cls_max_hits[q];
     uint64_t gcap = 64;
     while (gcap < 2 * hb) gcap <<= 1;
     if (gcap > kMaxTableSlots) {
@@ -901,17 +978,60 @@ static int plan_fused(const snap_index* idx, Engine* e, const uint64_t* d_offset
         return SNAP_E_INVAL;
     }
     if (gcap > (uint64_t)scap) {
+        // the tables themselves are allocated in plan_batch once every class is laid out
         const uint64_t per_warp = gcap * (sizeof(CandSlot) + sizeof(HitRec) / 2 + 2);
         const uint64_t max_warps = std::max<uint64_t>(1, e->overflow_budget / per_warp);
         if (blocks * warps > max_warps) blocks = std::max<uint64_t>(1, max_warps / warps);
-        const uint64_t tw = blocks * warps;
-        const uint64_t tslots = tw * gcap;
+        a.gcap = (uint32_t)gcap;
+        plan->table_slots[q] = blocks * warps * gcap;
+    }
+    if (seeds_global) {
+        DevBuf& gs = e->gseeds[q];
+        if ((rc = gs.ensure(blocks * warps * (uint64_t)a.seed_cap * sizeof(SeedRec),
+                            "seed records")))
+            return rc;
+        a.gseeds = static_cast<SeedRec*>(gs.p);
+    }
+    plan->kfn[q] = kfn;
+    plan->smem[q] = smem;
+    plan->blocks[q] = blocks;
+    plan->warps[q] = warps;
+    plan->use[q] = true;
+    return SNAP_OK;
+}
+
+static int plan_batch(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
+                      const snap_params* p, snap_result* d_out, const BatchPrep& bp,
+                      const LaunchShape& shape, BatchPlan* plan) {
+    int rc;
+    plan->shape = shape;
+    plan->light = bp.st.n_light > 0 && shape.light_threads > 0;
+    if ((rc = e->head.ensure(16 * sizeof(unsigned long long), "queue heads"))) return rc;
+    plan->head = static_cast<unsigned long long*>(e->head.p);
+    if ((rc = e->heavy.ensure(2 * n * sizeof(uint32_t), "read lists"))) return rc;
+    plan->heavy_ids = static_cast<uint32_t*>(e->heavy.p);
+    plan->cl.list = plan->heavy_ids + n;
+    plan->cl.count = plan->head + 5;
+    unsigned long long off = 0;
+    for (int q = 0; q < kClasses; ++q) {
+        plan->cl.off[q] = off;
+        off += bp.st.cls_n[q];
+    }
+    if (plan->light && (rc = light_prepare())) return rc;
+    for (int q = 0; q < kClasses; ++q)
+        if (bp.st.cls_n[q] > 0 &&
+            (rc = plan_class(idx, e, d_offsets, n, p, d_out, bp, shape, q, plan)))
+            return rc;
+    // global candidate tables: one buffer for the largest class need (the class
+    // launches run one after another and leave the tables empty)
+    uint64_t slots = 0;
+    for (int q = 0; q < kClasses; ++q) slots = std::max(slots, plan->table_slots[q]);
+    if (slots) {
         void* before = e->gtab.p;
         const size_t before_bytes = e->gtab.bytes;
-        if ((rc = e->gtab.ensure(tslots * sizeof(CandSlot), "overflow tables"))) return rc;
-        if ((rc = e->ghits.ensure(tw * (gcap / 2) * sizeof(HitRec), "overflow hits"))) return rc;
-        if ((rc = e->gdense.ensure(tw * (gcap / 2) * sizeof(uint32_t), "overflow lists")))
-            return rc;
+        if ((rc = e->gtab.ensure(slots * sizeof(CandSlot), "overflow tables"))) return rc;
+        if ((rc = e->ghits.ensure(slots / 2 * sizeof(HitRec), "overflow hits"))) return rc;
+        if ((rc = e->gdense.ensure(slots / 2 * sizeof(uint32_t), "overflow lists"))) return rc;
         if (e->gtab.p != before || e->gtab.bytes != before_bytes || !e->gtab_ready) {
             // fresh tables start empty; kernels keep them empty afterwards
             const uint64_t all = e->gtab.bytes / sizeof(CandSlot);
@@ -921,43 +1041,40 @@ static int plan_fused(const snap_index* idx, Engine* e, const uint64_t* d_offset
             SNAP_CUDA(cudaDeviceSynchronize(), "table init");
             e->gtab_ready = true;
         }
-        a.gtab = static_cast<CandSlot*>(e->gtab.p);
-        a.ghits = static_cast<HitRec*>(e->ghits.p);
-        a.gdense = static_cast<uint32_t*>(e->gdense.p);
-        a.gcap = (uint32_t)gcap;
+        for (int q = 0; q < kClasses; ++q) {
+            if (!plan->table_slots[q]) continue;
+            plan->a[q].gtab = static_cast<CandSlot*>(e->gtab.p);
+            plan->a[q].ghits = static_cast<HitRec*>(e->ghits.p);
+            plan->a[q].gdense = static_cast<uint32_t*>(e->gdense.p);
+        }
     }
-    if ((rc = e->head.ensure(64, "queue head"))) return rc;
-    a.head = static_cast<unsigned long long*>(e->head.p);
-    if (plan->light) {
-        if ((rc = e->heavy.ensure(n * sizeof(uint32_t), "read list"))) return rc;
-        a.order = static_cast<uint32_t*>(e->heavy.p);
-        a.n_items_dev = a.head + 1;
-        if ((rc = light_prepare())) return rc;
-    }
-    plan->kfn = kfn;
-    plan->smem = smem;
-    plan->blocks = blocks;
-    plan->shape = shape;
     return SNAP_OK;
 }
 
 // Enqueue the planned launch sequence on `stream` (allocation-free; capturable).
-static int enqueue_fused(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
+static int enqueue_batch(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
                          const snap_params* p, snap_result* d_out, cudaStream_t stream,
-                         const BatchPrep& bp, const FusedPlan& plan) {
+                         const BatchPrep& bp, const BatchPlan& plan) {
     int rc;
-    SNAP_CUDA(cudaMemsetAsync(plan.a.head, 0, sizeof(unsigned long long), stream), "head clear");
+    SNAP_CUDA(cudaMemsetAsync(plan.head, 0, 16 * sizeof(unsigned long long), stream),
+              "queue clear");
     if (plan.light) {
-        // short reads: one thread each; the warp kernel then takes the rest
-        if ((rc = launch_light(idx, e, d_offsets, n, p, d_out, stream, bp,
-                               const_cast<uint32_t*>(plan.a.order),
-                               const_cast<unsigned long long*>(plan.a.n_items_dev),
-                               plan.shape.light_threads)))
+        // short reads: one thread each; the leftovers go to the warp kernel
+        if ((rc = launch_light(idx, e, d_offsets, n, p, d_out, stream, bp, plan.heavy_ids,
+                               plan.head + 4, plan.shape.light_threads)))
             return rc;
     }
     e->launches++;
-    plan.kfn<<<(unsigned)plan.blocks, plan.shape.warps * 32, plan.smem, stream>>>(plan.a);
-    SNAP_CUDA(cudaGetLastError(), "align launch");
+    k_split_classes<<<grid_cap(e->sms, n, 256), 256, 0, stream>>>(
+        plan.light ? plan.heavy_ids : nullptr, plan.head + 4, n, d_offsets, plan.cl);
+    SNAP_CUDA(cudaGetLastError(), "split launch");
+    for (int q = 0; q < kClasses; ++q) {
+        if (!plan.use[q]) continue;
+        e->launches++;
+        plan.kfn[q]<<<(unsigned)plan.blocks[q], plan.warps[q] * 32, plan.smem[q], stream>>>(
+            plan.a[q]);
+        SNAP_CUDA(cudaGetLastError(), "align launch");
+    }
     return SNAP_OK;
 }
 
@@ -976,16 +1093,21 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
                        const snap_params* p, snap_result* d_out, cudaStream_t stream,
                        const BatchPrep& bp) {
     int rc;
+    // batches that share the classes present, the limits' register layout, the
+    // short-read bucket and the size within a factor of two share a tuned shape
     TuneKey key;
-    key.lvd = 0;  // the kernel variant follows from Lmax
+    key.lvd = 0;
+    for (int q = 0; q < kClasses; ++q)
+        if (bp.st.cls_n[q]) key.lvd |= 1 << q;
     key.light = bp.st.n_light > 0;
-    key.mmax = (int)bp.st.max_len;
-    key.Lmax = bp.st.max_L0;
-    key.nmax = bp.st.max_seeds;
-    key.hits = bp.st.max_hits_bound;
+    const int L = bp.st.max_L0;
+    key.mmax = 0;
+    key.Lmax = L <= 15 ? 15 : L <= 31 ? 31 : L <= 63 ? 63 : L <= 127 ? 127 : 1000;
+    key.nmax = 0;
+    key.hits = 0;
     int lg = 0;
     while ((1ull << lg) < n) ++lg;
-    key.nbucket = lg;  // batches within a factor of two share a tuned shape
+    key.nbucket = lg;
     LaunchShape shape = kShapes[0];
     bool tuned = false;
     for (const auto& t : e->tuned)
@@ -994,40 +1116,46 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
             tuned = true;
         }
     if (!tuned && e->autotune && n >= 4096) {
-        // time every candidate shape on this batch (results do not depend on it)
+        // time candidate shapes on this batch (results do not depend on the
+        // shape); give up on the search when one run is too slow to repeat
         if (!e->tev[0])
             for (auto& ev : e->tev) SNAP_CUDA(cudaEventCreate(&ev), "event create");
         float best_ms = 1e30f;
         for (const LaunchShape& cand : kShapes) {
             if (!key.light && cand.light_threads != kShapes[0].light_threads) continue;
-            FusedPlan tp;
-            if ((rc = plan_fused(idx, e, d_offsets, n, p, d_out, bp, cand, &tp))) return rc;
+            BatchPlan tp;
+            if ((rc = plan_batch(idx, e, d_offsets, n, p, d_out, bp, cand, &tp))) return rc;
             SNAP_CUDA(cudaEventRecord(e->tev[0], stream), "event");
-            if ((rc = enqueue_fused(idx, e, d_offsets, n, p, d_out, stream, bp, tp))) return rc;
+            if ((rc = enqueue_batch(idx, e, d_offsets, n, p, d_out, stream, bp, tp))) return rc;
             SNAP_CUDA(cudaEventRecord(e->tev[1], stream), "event");
             SNAP_CUDA(cudaEventSynchronize(e->tev[1]), "tune");
             float ms = 0;
             SNAP_CUDA(cudaEventElapsedTime(&ms, e->tev[0], e->tev[1]), "tune");
             if (ms < best_ms) {
                 best_ms = ms;
-                shape = tp.shape;
+                shape = cand;
             }
+            if (ms > 50.0f) break;
         }
         e->tuned.push_back({key, shape});
-        tuned = true;
     }
-    FusedPlan plan;
-    if ((rc = plan_fused(idx, e, d_offsets, n, p, d_out, bp, shape, &plan))) return rc;
-    e->last_shape = plan.shape;
+    BatchPlan plan;
+    if ((rc = plan_batch(idx, e, d_offsets, n, p, d_out, bp, shape, &plan))) return rc;
+    e->last_shape = shape;
+    for (int q = 0; q < kClasses; ++q)
+        if (plan.use[q]) {
+            e->last_shape.warps = plan.warps[q];
+            e->last_shape.scap = plan.a[q].scap;
+            break;
+        }
     e->last_graph = 0;
-    const int launches_before = (int)e->launches;
     if (e->use_graphs && stream != nullptr && stream != cudaStreamLegacy &&
         stream != cudaStreamPerThread) {
         // capture the launch sequence and replay it as one graph; an existing
         // executable graph is updated in place when only parameters changed
         cudaGraph_t g = nullptr;
         SNAP_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "capture");
-        rc = enqueue_fused(idx, e, d_offsets, n, p, d_out, stream, bp, plan);
+        rc = enqueue_batch(idx, e, d_offsets, n, p, d_out, stream, bp, plan);
         const cudaError_t ce = cudaStreamEndCapture(stream, &g);
         if (rc) {
             if (g) cudaGraphDestroy(g);
@@ -1056,9 +1184,8 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
         SNAP_CUDA(cudaGraphLaunch(e->gexec, stream), "graph launch");
         e->last_graph = 1;
     } else {
-        if ((rc = enqueue_fused(idx, e, d_offsets, n, p, d_out, stream, bp, plan))) return rc;
+        if ((rc = enqueue_batch(idx, e, d_offsets, n, p, d_out, stream, bp, plan))) return rc;
     }
-    (void)launches_before;
     return SNAP_OK;
 }
 
@@ -1340,7 +1467,7 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
     a.wx = up4((mmax + 15) / 16 + 4);
     a.wt = up4((mmax + Lmax + 15 + 15) / 16 + 4);
     a.seed_cap = nmax;
-    a.lv_ints = Lmax > 127 ? up4(2 * (2 * Lmax + 4)) : 0;
+    a.lv_ints = Lmax > 31 ? up4(2 * (2 * Lmax + 4)) : 0;
     const int fixed_words = 2 * a.wx + a.wt + 4 * a.seed_cap + a.lv_ints;
     int warps = 8;
     const int budget_words = 200 * 1024 / 4;

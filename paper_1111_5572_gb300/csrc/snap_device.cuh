@@ -277,15 +277,16 @@ __device__ inline int lv_warp_smem(const uint32_t* X, int m, const uint32_t* Tw,
     return kOver;
 }
 
-// Ra/Rb (2L+3 ints each) are required when L > 127; without them the call
-// flags kStInternal and reports kOver.
+// Up to L = 31 the diagonals live in registers (one or two per lane).  Beyond,
+// the shared-memory form spreads each round's 2e+1 active diagonals over all
+// lanes, which beats walking several register diagonals per lane every round.
+// Ra/Rb (2L+3 ints each) are required when L > 31; without them the call flags
+// kStInternal and reports kOver.
 __device__ __forceinline__ int lv_warp(const uint32_t* X, int m, const uint32_t* Tw, int tb, int n,
                                        int L, int lane, int* Ra, int* Rb, int* status) {
     if (L < 0) return kOver;
     if (L <= 15) return lv_warp_reg<1>(X, m, Tw, tb, n, L, lane);
     if (L <= 31) return lv_warp_reg<2>(X, m, Tw, tb, n, L, lane);
-    if (L <= 63) return lv_warp_reg<4>(X, m, Tw, tb, n, L, lane);
-    if (L <= 127) return lv_warp_reg<8>(X, m, Tw, tb, n, L, lane);
     if (Ra == nullptr) {
         if (lane == 0) atomicOr(status, kStInternal);
         return kOver;

@@ -32,6 +32,7 @@ struct Engine {
     cudaStream_t own_stream = nullptr;
     int sms = 0;
     DevBuf stats, head, packed, gtab, ghits, gdense, heavy;
+    DevBuf gseeds[4];  // per-class per-warp seed records of long reads
     bool gtab_ready = false;  // gtab holds only empty slots
     DevBuf h_reads, h_offsets, h_out, h_dmax;  // device copies for the host-buffer entry points
     PinnedBuf pin;

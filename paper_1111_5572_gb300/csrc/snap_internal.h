@@ -96,7 +96,18 @@ struct BatchStats {
     unsigned long long max_hits_bound;  // max over reads of n * h_max (capped)
     DevCounters ctr;
     unsigned long long n_light;  // reads short enough for the thread-per-read bucket
+    // per read-length class (see kClassBounds): reads and the maxima that size a launch
+    unsigned long long cls_n[4];
+    unsigned int cls_max_len[4];
+    int cls_max_L0[4];
+    int cls_max_seeds[4];
+    unsigned long long cls_max_hits[4];
 };
+// read-length classes of the warp-per-read kernel: m <= 256, <= 1024, <= 4096, longer
+constexpr int kClasses = 4;
+__host__ __device__ inline int length_class(uint64_t m) {
+    return (m > 256) + (m > 1024) + (m > 4096);
+}
 
 }  // namespace snapgpu
 

@@ -490,7 +490,7 @@ int align_plain(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uin
     auto up4 = [](int w) { return (w + 3) & ~3; };
     a.wx = up4((mmax + 15) / 16 + 4);
     a.wt = up4((mmax + Lmax + 30) / 16 + 4);
-    a.lv_ints = Lmax > 127 ? up4(2 * (2 * Lmax + 4)) : 0;
+    a.lv_ints = Lmax > 31 ? up4(2 * (2 * Lmax + 4)) : 0;
     a.warp_words = a.wx + a.wt + a.lv_ints;
     int warps = 8;
     while (warps > 1 && (size_t)warps * a.warp_words * 4 > 200 * 1024) warps >>= 1;
