@@ -232,6 +232,10 @@ typedef struct {
     int32_t warps_per_block;  /* batched form: warps per block of the warp-per-read kernel */
     int32_t table_slots;      /* batched form: shared candidate slots per warp */
     int32_t graph_replay;     /* 1 when the launch sequence ran as a CUDA graph */
+    int32_t team_classes;     /* read-length classes aligned in team mode (one read per
+                                 block, all warps of the block on each edit distance) */
+    uint64_t ed_filtered;     /* edit distances (counted in ed_calls and ed_over) proven
+                                 over the limit by the q-gram bound without the rounds */
 } snap_call_stats;
 
 int snap_last_call_stats(const snap_index* index, snap_call_stats* out);

@@ -59,7 +59,8 @@ class snap_call_stats(ctypes.Structure):
                 ("ed_calls", ctypes.c_uint64), ("ed_over", ctypes.c_uint64),
                 ("window_bytes", ctypes.c_uint64), ("light_threads", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("table_slots", ctypes.c_int32),
-                ("graph_replay", ctypes.c_int32)]
+                ("graph_replay", ctypes.c_int32), ("team_classes", ctypes.c_int32),
+                ("ed_filtered", ctypes.c_uint64)]
 
 
 _lib = None

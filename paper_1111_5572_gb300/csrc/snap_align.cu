@@ -284,6 +284,7 @@ struct FusedArgs {
     uint32_t* gdense; // per-warp dense slot lists, gcap / 2 each
     uint32_t gcap;
     SeedRec* gseeds;  // per-warp seed records (seed_cap each) when not in shared memory
+    uint32_t* gqbits; // per-warp q-gram bitmaps (2 x kQWords) for large limits, or NULL
     int* status;
     DevCounters* ctr;
     // per-warp shared-memory layout, in 32-bit words; every section offset is a
@@ -296,20 +297,21 @@ struct FusedArgs {
 struct WarpCounters {
     uint32_t seeds = 0, slot_reads = 0, list_entries = 0, ed_calls = 0, ed_over = 0;
     unsigned long long window_words = 0;
+    uint32_t ed_filtered = 0;
 };
 
 __device__ __forceinline__ void flush_counters(DevCounters* ctr, WarpCounters& c) {
-    unsigned long long v[6] = {c.seeds, c.slot_reads, c.list_entries, c.ed_calls, c.ed_over,
-                               c.window_words};
+    unsigned long long v[7] = {c.seeds, c.slot_reads, c.list_entries, c.ed_calls, c.ed_over,
+                               c.window_words, c.ed_filtered};
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < 7; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
     }
     if ((threadIdx.x & 31) == 0) {
         unsigned long long* dst = &ctr->seeds;
 #pragma unroll
-        for (int k = 0; k < 6; ++k)
+        for (int k = 0; k < 7; ++k)
             if (v[k]) atomicAdd(dst + k, v[k]);
     }
 }
@@ -327,16 +329,227 @@ struct WarpMem {
     CandSlot* gtab;
     HitRec* ghits;
     uint32_t* gdense;
+    uint32_t* qbits;  // q-gram bitmaps of the read, one per strand (or NULL: no filter)
+    int* job;         // team mode: the lead warp's posted job (see k_align_team)
 };
+
+// ---------------------------------------------------------------------------
+// q-gram rejection ahead of large-limit edit distances (the q-gram lemma).  If some prefix Y of
+// the window W has Lev(X, Y) <= L, then X and Y share at least
+// |X| - q + 1 - L*q q-grams (each edit touches at most q of X's q-grams, the
+// others reappear in Y), and Y's q-grams are among W's.  Counting the window
+// positions whose q-gram is in a bitmap of X's q-grams can only overcount that
+// shared number, so a count below the bound proves the distance is over L and
+// the rounds of the edit distance are skipped: the result is unchanged.
+// ---------------------------------------------------------------------------
+constexpr int kQ = 9;                          // q-gram length (18 bits: direct index)
+constexpr int kQWords = (1 << (2 * kQ)) / 32;  // presence bitmap words per strand
+constexpr int kQMinL = 48;                     // below this limit the rounds are cheap
+constexpr uint32_t kQMask = (1u << (2 * kQ)) - 1u;
+
+// Mark the q-grams of the packed sequence X (m bases) in bits (zero on entry).
+__device__ __forceinline__ void build_qbits(const uint32_t* X, int m, uint32_t* bits, int lane) {
+    for (int i = lane; i + kQ <= m; i += 32) {
+        const uint32_t g = get16(X, (uint64_t)i) & kQMask;
+        atomicOr(bits + (g >> 5), 1u << (g & 31));
+    }
+    __syncwarp();
+}
+
+// Zero the words build_qbits touched, leaving bits all zero again.
+__device__ __forceinline__ void clear_qbits(const uint32_t* X, int m, uint32_t* bits, int lane) {
+    __syncwarp();
+    for (int i = lane; i + kQ <= m; i += 32) bits[(get16(X, (uint64_t)i) & kQMask) >> 5] = 0u;
+    __syncwarp();
+}
+
+// Number of window positions whose q-gram is marked in bits.
+__device__ __forceinline__ int count_qhits(const uint32_t* Tw, int tb, int n, const uint32_t* bits,
+                                           int lane) {
+    // eight independent map loads in flight per lane (the map lives in L2)
+    constexpr int kU = 8;
+    const int npos = n - kQ + 1;
+    int c = 0;
+    for (int j0 = 0; j0 < npos; j0 += 32 * kU) {
+        uint32_t word[kU], bit[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int j = j0 + u * 32 + lane;
+            const uint32_t g = get16(Tw, (uint64_t)(tb + min(j, npos - 1))) & kQMask;
+            bit[u] = j < npos ? (g & 31) : 32u;
+            word[u] = __ldcg(bits + (g >> 5));
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) c += bit[u] < 32u ? (word[u] >> bit[u]) & 1u : 0u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    return c;
+}
+
+// Per-thread share of count_qhits over positions tid, tid + nt, ... (no reduction).
+__device__ __forceinline__ int count_qhits_part(const uint32_t* Tw, int tb, int n,
+                                                const uint32_t* bits, int tid, int nt) {
+    constexpr int kU = 4;
+    const int npos = n - kQ + 1;
+    int c = 0;
+    for (int j0 = 0; j0 < npos; j0 += nt * kU) {
+        uint32_t word[kU], bit[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int j = j0 + u * nt + tid;
+            const uint32_t g = get16(Tw, (uint64_t)(tb + min(j, npos - 1))) & kQMask;
+            bit[u] = j < npos ? (g & 31) : 32u;
+            word[u] = __ldcg(bits + (g >> 5));
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) c += bit[u] < 32u ? (word[u] >> bit[u]) & 1u : 0u;
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Team mode.  When a length class has too few reads to fill the SMs with one
+// warp per read, each block aligns one read at a time: its first warp (the
+// lead) runs the per-read logic exactly as in warp mode, and every edit
+// distance is computed by all warps of the block together.  The lead posts a
+// job (op, key, limit, read length, which strands' q-gram maps are built) in
+// shared memory and meets the helpers at a block barrier; all threads then run
+// team_distance, whose result is uniform over the block.
+// ---------------------------------------------------------------------------
+constexpr int kTeamWarps = 8;
+constexpr int kTeamReadsPerSm = 8;  // team mode below this many reads per SM
+enum : int { kJobExit = 0, kJobDistance = 1 };
+constexpr int kJobWords = 8;  // op, key lo, key hi, L, m, qbuilt, counter, pad
+
+// Landau-Vishkin rounds over the whole block: diagonals of round e spread over
+// all nt threads, one barrier per round (which also votes on completion).
+__device__ inline int lv_team(const uint32_t* X, int m, const uint32_t* Tw, int tb, int n, int L,
+                              int tid, int nt, int* Ra, int* Rb) {
+    constexpr int NEG = -0x40000000;
+    const int W = 2 * L + 3, off = L + 1;
+    for (int i = tid; i < W; i += nt) {
+        Ra[i] = NEG;
+        Rb[i] = NEG;
+    }
+    __syncthreads();
+    for (int e = 0; e <= L; ++e) {
+        int done = 0;
+        for (int idx = tid; idx < 2 * e + 1; idx += nt) {
+            const int k = idx - e;
+            int r;
+            if (e == 0) {
+                r = 0;
+            } else {
+                r = max(max(Ra[k + off] + 1, Ra[k + 1 + off] + 1), Ra[k - 1 + off]);
+            }
+            if (r > m) r = m;
+            if (r + k > n) r = n - k;
+            if (r < 0 || r + k < 0) {
+                r = NEG;
+            } else {
+                r = slide(X, m, Tw, tb, n, r, k);
+                done |= (r >= m);
+            }
+            Rb[k + off] = r;
+        }
+        if (__syncthreads_or(done)) return e;
+        int* t = Ra;
+        Ra = Rb;
+        Rb = t;
+    }
+    return kOver;
+}
+
+// The distance job, run by every thread of the block with the same arguments.
+// Returns the distance (kOver when over L) and sets *filtered when the q-gram
+// bound decided it; builds the q-gram map of the candidate's strand if needed.
+__device__ int team_distance(const FusedArgs& a, const WarpMem& wm, int m, unsigned long long key,
+                             int L, int qbuilt, int tid, int nt, bool* filtered) {
+    const uint64_t p = key >> 1;
+    const int strand = (int)(key & 1);
+    const uint64_t avail = a.G - p;
+    const int n_t = (int)min(avail, (uint64_t)(m + L));
+    const uint64_t w0 = p >> 4;
+    const int tb = (int)(p & 15);
+    const int nwt = (tb + n_t + 15) / 16 + 2;
+    const uint32_t* X = strand ? wm.Xr : wm.Xf;
+    for (int w = tid; w < nwt; w += nt) wm.Tw[w] = __ldg(a.genome + w0 + w);
+    const int bound = (m - kQ + 1) - L * kQ;
+    const bool use_q = wm.qbits && L >= kQMinL && bound > 0;
+    uint32_t* bits = wm.qbits ? wm.qbits + strand * kQWords : nullptr;
+    if (use_q && !(qbuilt & (1 << strand))) {
+        for (int i = tid; i + kQ <= m; i += nt) {
+            const uint32_t g = get16(X, (uint64_t)i) & kQMask;
+            atomicOr(bits + (g >> 5), 1u << (g & 31));
+        }
+    }
+    int* counter = wm.job + 6;
+    if (tid == 0) *counter = 0;
+    __syncthreads();
+    *filtered = false;
+    if (use_q) {
+        int c = count_qhits_part(wm.Tw, tb, n_t, bits, tid, nt);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+        if ((tid & 31) == 0) atomicAdd(counter, c);
+        __syncthreads();
+        if (*counter < bound) {
+            *filtered = true;
+            return kOver;
+        }
+    }
+    return lv_team(X, m, wm.Tw, tb, n_t, L, tid, nt, wm.lvA, wm.lvB);
+}
+
+// Helper warps of a team: run posted jobs until the lead posts kJobExit.
+__device__ void team_helper(const FusedArgs& a, const WarpMem& wm) {
+    for (;;) {
+        __syncthreads();  // job posted
+        const int op = wm.job[0];
+        if (op == kJobExit) return;
+        const unsigned long long key =
+            (unsigned long long)(uint32_t)wm.job[1] | ((unsigned long long)(uint32_t)wm.job[2] << 32);
+        const int L = wm.job[3], m = wm.job[4], qb = wm.job[5];
+        bool filtered;
+        team_distance(a, wm, m, key, L, qb, threadIdx.x, blockDim.x, &filtered);
+    }
+}
 
 // Edit distance of candidate `key` at limit L (warp-wide, result uniform).  LVD
 // selects the diagonal layout: D diagonals per lane in registers (L <= 32D/2 - 1)
 // or 0 for shared memory (any L).  One variant per kernel keeps the code small.
-template <int LVD>
+template <int LVD, bool TEAM>
 __device__ __forceinline__ int candidate_distance(const FusedArgs& a, const WarpMem& wm, int m,
                                                unsigned long long key, int L, int lane,
-                                               WarpCounters& wc) {
+                                               WarpCounters& wc, int& qbuilt) {
     if (L < 0) return kOver;
+    if constexpr (TEAM) {
+        // lead warp: post the job, then compute it with the helpers
+        if (lane == 0) {
+            wm.job[0] = kJobDistance;
+            wm.job[1] = (int)(uint32_t)key;
+            wm.job[2] = (int)(uint32_t)(key >> 32);
+            wm.job[3] = L;
+            wm.job[4] = m;
+            wm.job[5] = qbuilt;
+        }
+        __syncthreads();  // job posted
+        bool filtered;
+        const int d = team_distance(a, wm, m, key, L, qbuilt, threadIdx.x, blockDim.x, &filtered);
+        const int strand = (int)(key & 1);
+        if (wm.qbits && L >= kQMinL && (m - kQ + 1) - L * kQ > 0) qbuilt |= 1 << strand;
+        if (lane == 0) {
+            const uint64_t p = key >> 1;
+            const int n_t = (int)min(a.G - p, (uint64_t)(m + L));
+            wc.window_words += (unsigned)(((int)(p & 15) + n_t + 15) / 16 + 2);
+            wc.ed_calls++;
+            wc.ed_over += (d < 0);
+            wc.ed_filtered += filtered;
+        }
+        __syncwarp();
+        return d;
+    }
     const uint64_t p = key >> 1;
     const int strand = (int)(key & 1);
     const uint64_t avail = a.G - p;
@@ -350,8 +563,23 @@ __device__ __forceinline__ int candidate_distance(const FusedArgs& a, const Warp
     if constexpr (LVD > 0) {
         d = lv_warp_reg<LVD>(strand ? wm.Xr : wm.Xf, m, wm.Tw, tb, n_t, L, lane);
     } else {
-        d = lv_warp(strand ? wm.Xr : wm.Xf, m, wm.Tw, tb, n_t, L, lane, wm.lvA, wm.lvB,
-                    a.status);
+        bool rejected = false;
+        const int bound = (m - kQ + 1) - L * kQ;
+        if (wm.qbits && L >= kQMinL && bound > 0) {
+            uint32_t* bits = wm.qbits + strand * kQWords;
+            if (!(qbuilt & (1 << strand))) {
+                build_qbits(strand ? wm.Xr : wm.Xf, m, bits, lane);
+                qbuilt |= 1 << strand;
+            }
+            rejected = count_qhits(wm.Tw, tb, n_t, bits, lane) < bound;
+        }
+        if (rejected) {
+            d = kOver;
+            if (lane == 0) wc.ed_filtered++;
+        } else {
+            d = lv_warp(strand ? wm.Xr : wm.Xf, m, wm.Tw, tb, n_t, L, lane, wm.lvA, wm.lvB,
+                        a.status);
+        }
     }
     __syncwarp();
     if (lane == 0) {
@@ -362,7 +590,7 @@ __device__ __forceinline__ int candidate_distance(const FusedArgs& a, const Warp
     return d;
 }
 
-template <int LVD>
+template <int LVD, bool TEAM>
 __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem& wm, uint64_t r,
                                                int lane, WarpCounters& wc) {
     const uint64_t o0 = a.offsets[r], o1 = a.offsets[r + 1];
@@ -439,7 +667,8 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
             if (lane == 0) atomicOr(a.status, kStTableFull);
         }
         if (ok) {
-            int nd = 0;  // distinct candidates so far (slots listed in dense)
+            int nd = 0;      // distinct candidates so far (slots listed in dense)
+            int qbuilt = 0;  // strands whose q-gram bitmap is built for this read
             int d_best = kInf, d_second = kInf, nh = 0, t = 0;
             unsigned long long best_key = 0;
             bool any_nonpopular = false, returned = false;
@@ -453,7 +682,7 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                 const uint32_t slot = (uint32_t)(packed & 0xfffffu);
                 const unsigned long long key = kKeyMask - ((packed >> 20) & kKeyMask);
                 const int L = limit();
-                const int d = candidate_distance<LVD>(a, wm, m, key, L, lane, wc);
+                const int d = candidate_distance<LVD, TEAM>(a, wm, m, key, L, lane, wc, qbuilt);
                 if (lane == 0) {
                     tab[slot].state = d >= 0 ? d : kOver;
                     if (d >= 0) {
@@ -553,9 +782,11 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                 res_strand = (int)(best_key & 1);
                 res_d = d_best;
             }
-            // leave the table empty for the next read
+            // leave the table and the q-gram maps empty for the next read
             __syncwarp();
             for (int j = lane; j < nd; j += 32) tab[dense[j]] = empty_slot();
+            if (qbuilt & 1) clear_qbits(wm.Xf, m, wm.qbits, lane);
+            if (qbuilt & 2) clear_qbits(wm.Xr, m, wm.qbits + kQWords, lane);
             __syncwarp();
         }
     }
@@ -589,6 +820,7 @@ __global__ void __launch_bounds__(256, 4) k_align_fused(FusedArgs a) {
     wm.gtab = a.gtab ? a.gtab + gw * a.gcap : nullptr;
     wm.ghits = a.ghits ? a.ghits + gw * (a.gcap / 2) : nullptr;
     wm.gdense = a.gdense ? a.gdense + gw * (a.gcap / 2) : nullptr;
+    wm.qbits = a.gqbits ? a.gqbits + gw * (2 * kQWords) : nullptr;
     for (int j = lane; j < a.scap; j += 32) wm.stab[j] = empty_slot();
     __syncwarp();
     WarpCounters wc;
@@ -599,8 +831,51 @@ __global__ void __launch_bounds__(256, 4) k_align_fused(FusedArgs a) {
         it = __shfl_sync(kFull, it, 0);
         if (it >= n_items) break;
         const uint64_t r = a.order ? a.order[it] : it;
-        align_one_read<LVD>(a, wm, r, lane, wc);
+        align_one_read<LVD, false>(a, wm, r, lane, wc);
     }
+    flush_counters(a.ctr, wc);
+}
+
+// Team mode (see team_distance): one read per block at a time, kTeamWarps warps;
+// warp 0 leads, the shared-memory layout is that of one warp plus the job words.
+__global__ void __launch_bounds__(kTeamWarps * 32) k_align_team(FusedArgs a) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    WarpMem wm;
+    wm.Xf = smem;
+    wm.Xr = smem + a.off_xr;
+    wm.Tw = smem + a.off_tw;
+    wm.seeds = a.gseeds ? a.gseeds + (uint64_t)blockIdx.x * a.seed_cap
+                        : reinterpret_cast<SeedRec*>(smem + a.off_seeds);
+    wm.stab = reinterpret_cast<CandSlot*>(smem + a.off_tab);
+    wm.shits = reinterpret_cast<HitRec*>(smem + a.off_hits);
+    wm.sdense = smem + a.off_dense;
+    wm.lvA = reinterpret_cast<int*>(smem + a.off_lv);
+    wm.lvB = wm.lvA + a.lv_ints / 2;
+    const uint64_t gw = blockIdx.x;
+    wm.gtab = a.gtab ? a.gtab + gw * a.gcap : nullptr;
+    wm.ghits = a.ghits ? a.ghits + gw * (a.gcap / 2) : nullptr;
+    wm.gdense = a.gdense ? a.gdense + gw * (a.gcap / 2) : nullptr;
+    wm.qbits = a.gqbits ? a.gqbits + gw * (2 * kQWords) : nullptr;
+    wm.job = reinterpret_cast<int*>(smem + a.warp_words);
+    if (wib != 0) {
+        team_helper(a, wm);
+        return;
+    }
+    for (int j = lane; j < a.scap; j += 32) wm.stab[j] = empty_slot();
+    __syncwarp();
+    WarpCounters wc;
+    const unsigned long long n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(a.head, 1ull);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= n_items) break;
+        const uint64_t r = a.order ? a.order[it] : it;
+        align_one_read<0, true>(a, wm, r, lane, wc);
+    }
+    if (lane == 0) wm.job[0] = kJobExit;
+    __syncthreads();  // releases the helpers
     flush_counters(a.ctr, wc);
 }
 
@@ -619,6 +894,7 @@ static FusedKernel fused_kernel_for(int Lmax) {
 // ---------------------------------------------------------------------------
 int DevBuf::ensure(size_t need, const char* what) {
     if (need <= bytes && p) return SNAP_OK;
+    std::lock_guard<std::recursive_mutex> lock(capture_alloc_mutex());
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
@@ -634,12 +910,14 @@ int DevBuf::ensure(size_t need, const char* what) {
     return SNAP_OK;
 }
 void DevBuf::release() {
+    std::lock_guard<std::recursive_mutex> lock(capture_alloc_mutex());
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
 }
 int PinnedBuf::ensure(size_t need, const char* what) {
     if (need <= bytes && p) return SNAP_OK;
+    std::lock_guard<std::recursive_mutex> lock(capture_alloc_mutex());
     if (p) cudaFreeHost(p);
     p = nullptr;
     bytes = 0;
@@ -655,6 +933,7 @@ int PinnedBuf::ensure(size_t need, const char* what) {
     return SNAP_OK;
 }
 void PinnedBuf::release() {
+    std::lock_guard<std::recursive_mutex> lock(capture_alloc_mutex());
     if (p) cudaFreeHost(p);
     p = nullptr;
     bytes = 0;
@@ -674,6 +953,7 @@ Engine* engine_create() {
 void engine_destroy(Engine* e) {
     if (!e) return;
     for (DevBuf& b : e->gseeds) b.release();
+    for (DevBuf& b : e->gqbits) b.release();
     for (DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->gdense,
                       &e->heavy, &e->h_reads, &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds,
                       &e->p_hits,
@@ -695,6 +975,7 @@ void engine_destroy(Engine* e) {
 size_t engine_bytes(const Engine* e) {
     size_t s = 0;
     for (const DevBuf& b : e->gseeds) s += b.bytes;
+    for (const DevBuf& b : e->gqbits) s += b.bytes;
     for (const DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->gdense,
                             &e->heavy,
                             &e->h_reads, &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds,
@@ -706,6 +987,7 @@ size_t engine_bytes(const Engine* e) {
 
 void engine_release(Engine* e) {
     for (DevBuf& b : e->gseeds) b.release();
+    for (DevBuf& b : e->gqbits) b.release();
     if (e->gexec) {
         cudaGraphExecDestroy(e->gexec);  // it points into the workspaces
         e->gexec = nullptr;
@@ -866,10 +1148,12 @@ static int finish_status(Engine* e, cudaStream_t stream, const char* where, uint
     L.ed_calls = h->ctr.ed_calls;
     L.ed_over = h->ctr.ed_over;
     L.window_bytes = h->ctr.window_words * 4;
+    L.ed_filtered = h->ctr.ed_filtered;
     L.light_threads = e->last_shape.light_threads;
     L.warps_per_block = e->last_shape.warps;
     L.table_slots = e->last_shape.scap;
     L.graph_replay = e->last_graph;
+    L.team_classes = e->last_team;
     return SNAP_OK;
 }
 
@@ -884,7 +1168,8 @@ struct BatchPlan {
     FusedKernel kfn[kClasses] = {nullptr, nullptr, nullptr, nullptr};
     size_t smem[kClasses] = {0, 0, 0, 0};
     uint64_t blocks[kClasses] = {0, 0, 0, 0};
-    int warps[kClasses] = {0, 0, 0, 0};
+    int warps[kClasses] = {0, 0, 0, 0};    // reads in flight per block
+    int threads[kClasses] = {0, 0, 0, 0};  // threads per block
     ClassLists cl;
     uint32_t* heavy_ids = nullptr;
     unsigned long long* head = nullptr;  // [0..3] class queue heads, [4] leftovers, [5..8] class counts
@@ -895,7 +1180,7 @@ struct BatchPlan {
 // happens after planning, so the enqueue can be captured).
 static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
                       const snap_params* p, snap_result* d_out, const BatchPrep& bp,
-                      const LaunchShape& shape, int q, BatchPlan* plan) {
+                      const LaunchShape& shape, int q, cudaStream_t stream, BatchPlan* plan) {
     int rc;
     FusedArgs& a = plan->a[q];
     memset(&a, 0, sizeof(a));
@@ -934,7 +1219,11 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     const int seed_words = seeds_global ? 0 : 4 * a.seed_cap;
     const int fixed_words = 2 * a.wx + a.wt + seed_words + a.lv_ints;
     const int budget_words = 200 * 1024 / 4;  // per block; 7 words per table slot
-    int warps = std::max(1, shape.warps);
+    // a class of large limits with too few reads to give each SM several warps
+    // runs in team mode (a block per read); `warps` counts the per-read warps
+    // (lead warps) of a block, which own the per-warp layout below
+    const bool team = Lmax > 31 && bp.st.cls_n[q] < (uint64_t)e->sms * kTeamReadsPerSm;
+    int warps = team ? 1 : std::max(1, shape.warps);
     // a class with few reads spreads them over all SMs (one warp per read)
     while (warps > 1 && bp.st.cls_n[q] < (uint64_t)e->sms * warps) warps >>= 1;
     while (warps > 1 && warps * (fixed_words + 7 * 64) > budget_words) warps >>= 1;
@@ -953,16 +1242,17 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
         set_error("snap_align: internal shared-memory layout is not 16-byte aligned");
         return SNAP_E_INTERNAL;
     }
-    const size_t smem = (size_t)warps * a.warp_words * 4;
+    const size_t smem = (size_t)warps * a.warp_words * 4 + (team ? kJobWords * 4 : 0);
     if (smem > 227 * 1024) {
         set_error("snap_align: read length %d needs %zu bytes of shared memory per warp", mmax,
                   (size_t)a.warp_words * 4);
         return SNAP_E_INVAL;
     }
-    const FusedKernel kfn = fused_kernel_for(Lmax);
+    const FusedKernel kfn = team ? k_align_team : fused_kernel_for(Lmax);
+    const int threads = team ? kTeamWarps * 32 : warps * 32;
     if ((rc = raise_smem_limit((const void*)kfn, smem))) return rc;
     int per_sm = 0;
-    SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem),
+    SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem),
               "occupancy");
     if (per_sm < 1) per_sm = 1;
     uint64_t blocks = (uint64_t)e->sms * per_sm;
@@ -985,6 +1275,17 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
         a.gcap = (uint32_t)gcap;
         plan->table_slots[q] = blocks * warps * gcap;
     }
+    if (Lmax >= kQMinL && mmax >= 2 * kQ) {
+        // presence maps start zero; kernels clear what they set before the next read
+        DevBuf& gq = e->gqbits[q];
+        void* before = gq.p;
+        const size_t before_bytes = gq.bytes;
+        if ((rc = gq.ensure(blocks * warps * 2ull * kQWords * sizeof(uint32_t), "q-gram maps")))
+            return rc;
+        if (gq.p != before || gq.bytes != before_bytes)
+            SNAP_CUDA(cudaMemsetAsync(gq.p, 0, gq.bytes, stream), "q-gram map init");
+        a.gqbits = static_cast<uint32_t*>(gq.p);
+    }
     if (seeds_global) {
         DevBuf& gs = e->gseeds[q];
         if ((rc = gs.ensure(blocks * warps * (uint64_t)a.seed_cap * sizeof(SeedRec),
@@ -996,13 +1297,14 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     plan->smem[q] = smem;
     plan->blocks[q] = blocks;
     plan->warps[q] = warps;
+    plan->threads[q] = threads;
     plan->use[q] = true;
     return SNAP_OK;
 }
 
 static int plan_batch(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
                       const snap_params* p, snap_result* d_out, const BatchPrep& bp,
-                      const LaunchShape& shape, BatchPlan* plan) {
+                      const LaunchShape& shape, cudaStream_t stream, BatchPlan* plan) {
     int rc;
     plan->shape = shape;
     plan->light = bp.st.n_light > 0 && shape.light_threads > 0;
@@ -1020,7 +1322,7 @@ static int plan_batch(const snap_index* idx, Engine* e, const uint64_t* d_offset
     if (plan->light && (rc = light_prepare())) return rc;
     for (int q = 0; q < kClasses; ++q)
         if (bp.st.cls_n[q] > 0 &&
-            (rc = plan_class(idx, e, d_offsets, n, p, d_out, bp, shape, q, plan)))
+            (rc = plan_class(idx, e, d_offsets, n, p, d_out, bp, shape, q, stream, plan)))
             return rc;
     // global candidate tables: one buffer for the largest class need (the class
     // launches run one after another and leave the tables empty)
@@ -1035,10 +1337,9 @@ static int plan_batch(const snap_index* idx, Engine* e, const uint64_t* d_offset
         if (e->gtab.p != before || e->gtab.bytes != before_bytes || !e->gtab_ready) {
             // fresh tables start empty; kernels keep them empty afterwards
             const uint64_t all = e->gtab.bytes / sizeof(CandSlot);
-            k_init_ctab<<<grid_cap(e->sms, all, 256), 256>>>(static_cast<CandSlot*>(e->gtab.p),
-                                                            all);
+            k_init_ctab<<<grid_cap(e->sms, all, 256), 256, 0, stream>>>(
+                static_cast<CandSlot*>(e->gtab.p), all);
             SNAP_CUDA(cudaGetLastError(), "table init");
-            SNAP_CUDA(cudaDeviceSynchronize(), "table init");
             e->gtab_ready = true;
         }
         for (int q = 0; q < kClasses; ++q) {
@@ -1071,7 +1372,7 @@ static int enqueue_batch(const snap_index* idx, Engine* e, const uint64_t* d_off
     for (int q = 0; q < kClasses; ++q) {
         if (!plan.use[q]) continue;
         e->launches++;
-        plan.kfn[q]<<<(unsigned)plan.blocks[q], plan.warps[q] * 32, plan.smem[q], stream>>>(
+        plan.kfn[q]<<<(unsigned)plan.blocks[q], plan.threads[q], plan.smem[q], stream>>>(
             plan.a[q]);
         SNAP_CUDA(cudaGetLastError(), "align launch");
     }
@@ -1124,7 +1425,7 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
         for (const LaunchShape& cand : kShapes) {
             if (!key.light && cand.light_threads != kShapes[0].light_threads) continue;
             BatchPlan tp;
-            if ((rc = plan_batch(idx, e, d_offsets, n, p, d_out, bp, cand, &tp))) return rc;
+            if ((rc = plan_batch(idx, e, d_offsets, n, p, d_out, bp, cand, stream, &tp))) return rc;
             SNAP_CUDA(cudaEventRecord(e->tev[0], stream), "event");
             if ((rc = enqueue_batch(idx, e, d_offsets, n, p, d_out, stream, bp, tp))) return rc;
             SNAP_CUDA(cudaEventRecord(e->tev[1], stream), "event");
@@ -1140,23 +1441,29 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
         e->tuned.push_back({key, shape});
     }
     BatchPlan plan;
-    if ((rc = plan_batch(idx, e, d_offsets, n, p, d_out, bp, shape, &plan))) return rc;
+    if ((rc = plan_batch(idx, e, d_offsets, n, p, d_out, bp, shape, stream, &plan))) return rc;
     e->last_shape = shape;
     for (int q = 0; q < kClasses; ++q)
         if (plan.use[q]) {
-            e->last_shape.warps = plan.warps[q];
+            e->last_shape.warps = plan.threads[q] / 32;
             e->last_shape.scap = plan.a[q].scap;
             break;
         }
+    e->last_team = 0;
+    for (int q = 0; q < kClasses; ++q) e->last_team += plan.use[q] && plan.kfn[q] == k_align_team;
     e->last_graph = 0;
     if (e->use_graphs && stream != nullptr && stream != cudaStreamLegacy &&
         stream != cudaStreamPerThread) {
         // capture the launch sequence and replay it as one graph; an existing
         // executable graph is updated in place when only parameters changed
         cudaGraph_t g = nullptr;
-        SNAP_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "capture");
-        rc = enqueue_batch(idx, e, d_offsets, n, p, d_out, stream, bp, plan);
-        const cudaError_t ce = cudaStreamEndCapture(stream, &g);
+        cudaError_t ce;
+        {
+            std::lock_guard<std::recursive_mutex> lock(capture_alloc_mutex());
+            SNAP_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "capture");
+            rc = enqueue_batch(idx, e, d_offsets, n, p, d_out, stream, bp, plan);
+            ce = cudaStreamEndCapture(stream, &g);
+        }
         if (rc) {
             if (g) cudaGraphDestroy(g);
             return rc;
@@ -1210,6 +1517,9 @@ int align_batch_device(const snap_index* idx, Engine* e, const uint8_t* d_reads,
         return SNAP_E_INVAL;
     }
     const char* where = plain ? "snap_align_plain" : "snap_align";
+    e->last_shape = LaunchShape{0, 0, 0};  // set again by the batched form
+    e->last_graph = 0;
+    e->last_team = 0;
     BatchPrep bp;
     if ((rc = prepare_batch(idx, e, d_reads, d_offsets, n, p, stream, &bp, where))) return rc;
     rc = plain ? align_plain(idx, e, d_offsets, n, p, d_out, stream, bp)

@@ -29,6 +29,11 @@ int cuda_fail(cudaError_t e, const char* what) {
 // The dynamic shared-memory limit is a property of the kernel for the whole
 // process; concurrent callers with different layouts must never lower it under
 // each other's launches, so it only grows.
+std::recursive_mutex& capture_alloc_mutex() {
+    static std::recursive_mutex mu;
+    return mu;
+}
+
 int raise_smem_limit(const void* func, size_t bytes) {
     static std::mutex mu;
     static std::map<std::pair<int, const void*>, size_t> limit;

@@ -33,6 +33,7 @@ struct Engine {
     int sms = 0;
     DevBuf stats, head, packed, gtab, ghits, gdense, heavy;
     DevBuf gseeds[4];  // per-class per-warp seed records of long reads
+    DevBuf gqbits[4];  // per-class per-warp q-gram bitmaps (large limits)
     bool gtab_ready = false;  // gtab holds only empty slots
     DevBuf h_reads, h_offsets, h_out, h_dmax;  // device copies for the host-buffer entry points
     PinnedBuf pin;
@@ -48,6 +49,7 @@ struct Engine {
     cudaGraphExec_t gexec = nullptr;
     LaunchShape last_shape{0, 0, 0};
     int last_graph = 0;
+    int last_team = 0;  // classes of the last batch that ran in team mode
     uint64_t overflow_budget = 4ull << 30;  // device bytes for per-warp global candidate tables
     // plain-form workspace
     DevBuf p_seeds, p_hits, p_hitoff, p_partial, p_table, p_events, p_hitlist, p_items, p_misc,

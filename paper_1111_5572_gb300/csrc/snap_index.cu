@@ -190,6 +190,7 @@ using namespace snapgpu;
 extern "C" int snap_index_build(const uint8_t* genome_ascii, uint64_t genome_len, int seed_len,
                                 snap_index** out) {
     clear_error();
+    std::lock_guard<std::recursive_mutex> lock(capture_alloc_mutex());
     if (!out) {
         set_error("snap_index_build: out is NULL");
         return SNAP_E_INVAL;
@@ -321,6 +322,7 @@ extern "C" int snap_index_build(const uint8_t* genome_ascii, uint64_t genome_len
 extern "C" int snap_index_free(snap_index* idx) {
     clear_error();
     if (!idx) return SNAP_OK;
+    std::lock_guard<std::recursive_mutex> lock(capture_alloc_mutex());
     if (idx->engine) engine_destroy(idx->engine);
     cudaFree(idx->genome_words);
     cudaFree(idx->slots);

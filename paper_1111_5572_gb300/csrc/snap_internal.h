@@ -83,7 +83,8 @@ struct HitRec {
 
 // Traffic counters accumulated by the align kernels (one atomicAdd per warp).
 struct DevCounters {
-    unsigned long long seeds, slot_reads, list_entries, ed_calls, ed_over, window_words;
+    unsigned long long seeds, slot_reads, list_entries, ed_calls, ed_over, window_words,
+        ed_filtered;
 };
 
 // Statistics of a read batch, computed on the device before the main launch.
@@ -139,6 +140,12 @@ void set_error(const char* fmt, ...);
 void clear_error();
 int cuda_fail(cudaError_t e, const char* what);
 int raise_smem_limit(const void* func, size_t bytes);  // never lowers it
+
+// Held while a stream is being captured into a CUDA graph and around every
+// device or pinned allocation and free.  cudaFree / cudaFreeHost wait for the
+// whole device, which would be an implicit synchronisation with a stream that
+// another thread (a serving slot) is capturing and would invalidate its graph.
+std::recursive_mutex& capture_alloc_mutex();
 
 #define SNAP_CUDA(call, what)                                  \
     do {                                                       \
