@@ -251,9 +251,16 @@ int snap_last_call_stats(const snap_index* index, snap_call_stats* out);
  *   cuda_graphs  capture the per-batch launch sequence and replay it as one CUDA
  *                graph, updated in place between calls (only on a stream other
  *                than the legacy or per-thread default stream).
- * Passing autotune = 0 also forgets tuned shapes.
+ *   team         how a read-length class whose limits exceed 31 is aligned:
+ *                -1 (default) picks per batch, team mode when the class has fewer
+ *                than max(8, longest read / 12) reads per SM, else one warp per
+ *                read; 0 always one warp per read; 1 always team mode (one read
+ *                per block of 8 warps, all of them on each edit distance).
+ *                Results never depend on it.
+ * Passing autotune = 0 also forgets tuned shapes.  Returns SNAP_E_INVAL for a
+ * NULL index or team outside -1..1.
  */
-int snap_index_configure(snap_index* index, int autotune, int cuda_graphs);
+int snap_index_configure(snap_index* index, int autotune, int cuda_graphs, int team);
 
 /* Message for the last failed call on this thread ("" if none). */
 const char* snap_last_error(void);

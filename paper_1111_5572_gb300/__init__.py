@@ -90,7 +90,7 @@ def load_library(path: str = LIB_PATH):
     lib.snap_server_wait.argtypes = [vp, u64, vp, P(ctypes.c_double)]
     lib.snap_server_destroy.argtypes = [vp]
     lib.snap_last_call_stats.argtypes = [vp, P(snap_call_stats)]
-    lib.snap_index_configure.argtypes = [vp, i32, i32]
+    lib.snap_index_configure.argtypes = [vp, i32, i32, i32]
     lib.snap_last_error.argtypes = []
     lib.snap_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -138,9 +138,11 @@ class Index:
         _check(load_library().snap_index_info_get(self._h, ctypes.byref(inf)), "info")
         return {f: getattr(inf, f) for f, _ in snap_index_info._fields_ if f != "reserved"}
 
-    def configure(self, autotune: bool = True, cuda_graphs: bool = True):
-        """snap_index_configure: autotuning of launch shapes and CUDA-graph replay."""
-        _check(load_library().snap_index_configure(self._h, int(autotune), int(cuda_graphs)),
+    def configure(self, autotune: bool = True, cuda_graphs: bool = True, team: int = -1):
+        """snap_index_configure: autotuning of launch shapes, CUDA-graph replay and team
+        mode of long-read classes (-1 chosen per batch, 0 never, 1 always)."""
+        _check(load_library().snap_index_configure(self._h, int(autotune), int(cuda_graphs),
+                                                   int(team)),
                "snap_index_configure")
 
     def last_call_stats(self) -> dict:

@@ -345,6 +345,13 @@ struct WarpMem {
 constexpr int kQ = 9;                          // q-gram length (18 bits: direct index)
 constexpr int kQWords = (1 << (2 * kQ)) / 32;  // presence bitmap words per strand
 constexpr int kQMinL = 48;                     // below this limit the rounds are cheap
+
+// Whether the bound is tried: it must be able to fire (a positive bound), and
+// the over-limit rounds it can save (about L^2 diagonal steps) must outweigh
+// counting the window's m + L positions.
+__host__ __device__ __forceinline__ bool use_qfilter(int m, int L) {
+    return L >= kQMinL && (m - kQ + 1) - L * kQ > 0 && L * L >= 8 * (m + L);
+}
 constexpr uint32_t kQMask = (1u << (2 * kQ)) - 1u;
 
 // Mark the q-grams of the packed sequence X (m bases) in bits (zero on entry).
@@ -366,8 +373,8 @@ __device__ __forceinline__ void clear_qbits(const uint32_t* X, int m, uint32_t* 
 // Number of window positions whose q-gram is marked in bits.
 __device__ __forceinline__ int count_qhits(const uint32_t* Tw, int tb, int n, const uint32_t* bits,
                                            int lane) {
-    // eight independent map loads in flight per lane (the map lives in L2)
-    constexpr int kU = 8;
+    // several independent map loads in flight per lane (the map lives in L2)
+    constexpr int kU = 4;
     const int npos = n - kQ + 1;
     int c = 0;
     for (int j0 = 0; j0 < npos; j0 += 32 * kU) {
@@ -385,6 +392,18 @@ __device__ __forceinline__ int count_qhits(const uint32_t* Tw, int tb, int n, co
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
     return c;
+}
+
+// Warp form of the bound for candidate (strand, window at tb of n bases): builds
+// the strand's map on first use.
+__device__ __forceinline__ bool qgram_rejects(const WarpMem& wm, int m, int strand, int tb, int n,
+                                           int L, int lane, int& qbuilt) {
+    uint32_t* bits = wm.qbits + strand * kQWords;
+    if (!(qbuilt & (1 << strand))) {
+        build_qbits(strand ? wm.Xr : wm.Xf, m, bits, lane);
+        qbuilt |= 1 << strand;
+    }
+    return count_qhits(wm.Tw, tb, n, bits, lane) < (m - kQ + 1) - L * kQ;
 }
 
 // Per-thread share of count_qhits over positions tid, tid + nt, ... (no reduction).
@@ -418,7 +437,10 @@ __device__ __forceinline__ int count_qhits_part(const uint32_t* Tw, int tb, int 
 // team_distance, whose result is uniform over the block.
 // ---------------------------------------------------------------------------
 constexpr int kTeamWarps = 8;
-constexpr int kTeamReadsPerSm = 8;  // team mode below this many reads per SM
+// team mode below max(8, longest read / 12) reads per SM: per-read work grows
+// with the square of the limit, and one warp per read leaves long reads (and the
+// slowest read of the class) latency-bound
+constexpr int kTeamReadsPerSm = 8;
 enum : int { kJobExit = 0, kJobDistance = 1 };
 constexpr int kJobWords = 8;  // op, key lo, key hi, L, m, qbuilt, counter, pad
 
@@ -476,7 +498,7 @@ __device__ int team_distance(const FusedArgs& a, const WarpMem& wm, int m, unsig
     const uint32_t* X = strand ? wm.Xr : wm.Xf;
     for (int w = tid; w < nwt; w += nt) wm.Tw[w] = __ldg(a.genome + w0 + w);
     const int bound = (m - kQ + 1) - L * kQ;
-    const bool use_q = wm.qbits && L >= kQMinL && bound > 0;
+    const bool use_q = wm.qbits && use_qfilter(m, L);
     uint32_t* bits = wm.qbits ? wm.qbits + strand * kQWords : nullptr;
     if (use_q && !(qbuilt & (1 << strand))) {
         for (int i = tid; i + kQ <= m; i += nt) {
@@ -517,8 +539,9 @@ __device__ void team_helper(const FusedArgs& a, const WarpMem& wm) {
 }
 
 // Edit distance of candidate `key` at limit L (warp-wide, result uniform).  LVD
-// selects the diagonal layout: D diagonals per lane in registers (L <= 32D/2 - 1)
-// or 0 for shared memory (any L).  One variant per kernel keeps the code small.
+// selects the diagonal layout: D diagonals per lane in registers (L <= 32D/2 - 1),
+// 0 for shared memory (any L), or -1 for shared memory behind the q-gram bound.
+// One variant per kernel keeps the code small.
 template <int LVD, bool TEAM>
 __device__ __forceinline__ int candidate_distance(const FusedArgs& a, const WarpMem& wm, int m,
                                                unsigned long long key, int L, int lane,
@@ -538,7 +561,7 @@ __device__ __forceinline__ int candidate_distance(const FusedArgs& a, const Warp
         bool filtered;
         const int d = team_distance(a, wm, m, key, L, qbuilt, threadIdx.x, blockDim.x, &filtered);
         const int strand = (int)(key & 1);
-        if (wm.qbits && L >= kQMinL && (m - kQ + 1) - L * kQ > 0) qbuilt |= 1 << strand;
+        if (wm.qbits && use_qfilter(m, L)) qbuilt |= 1 << strand;
         if (lane == 0) {
             const uint64_t p = key >> 1;
             const int n_t = (int)min(a.G - p, (uint64_t)(m + L));
@@ -564,15 +587,9 @@ __device__ __forceinline__ int candidate_distance(const FusedArgs& a, const Warp
         d = lv_warp_reg<LVD>(strand ? wm.Xr : wm.Xf, m, wm.Tw, tb, n_t, L, lane);
     } else {
         bool rejected = false;
-        const int bound = (m - kQ + 1) - L * kQ;
-        if (wm.qbits && L >= kQMinL && bound > 0) {
-            uint32_t* bits = wm.qbits + strand * kQWords;
-            if (!(qbuilt & (1 << strand))) {
-                build_qbits(strand ? wm.Xr : wm.Xf, m, bits, lane);
-                qbuilt |= 1 << strand;
-            }
-            rejected = count_qhits(wm.Tw, tb, n_t, bits, lane) < bound;
-        }
+        if constexpr (LVD < 0)
+            rejected = wm.qbits && use_qfilter(m, L) &&
+                       qgram_rejects(wm, m, strand, tb, n_t, L, lane, qbuilt);
         if (rejected) {
             d = kOver;
             if (lane == 0) wc.ed_filtered++;
@@ -882,11 +899,12 @@ __global__ void __launch_bounds__(kTeamWarps * 32) k_align_team(FusedArgs a) {
 using FusedKernel = void (*)(FusedArgs);
 
 // The kernel variant for a batch whose largest limit is Lmax: one or two
-// register diagonals per lane when they cover [-Lmax, Lmax], else shared memory.
-static FusedKernel fused_kernel_for(int Lmax) {
+// register diagonals per lane when they cover [-Lmax, Lmax], else shared memory,
+// with the q-gram bound when some read of the class can use it (qmaps).
+static FusedKernel fused_kernel_for(int Lmax, bool qmaps = false) {
     if (Lmax <= 15) return k_align_fused<1>;
     if (Lmax <= 31) return k_align_fused<2>;
-    return k_align_fused<0>;
+    return qmaps ? k_align_fused<-1> : k_align_fused<0>;
 }
 
 // ---------------------------------------------------------------------------
@@ -1222,7 +1240,8 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     // a class of large limits with too few reads to give each SM several warps
     // runs in team mode (a block per read); `warps` counts the per-read warps
     // (lead warps) of a block, which own the per-warp layout below
-    const bool team = Lmax > 31 && bp.st.cls_n[q] < (uint64_t)e->sms * kTeamReadsPerSm;
+    const uint64_t team_below = (uint64_t)e->sms * std::max(kTeamReadsPerSm, mmax / 12);
+    const bool team = Lmax > 31 && (e->team < 0 ? bp.st.cls_n[q] < team_below : e->team == 1);
     int warps = team ? 1 : std::max(1, shape.warps);
     // a class with few reads spreads them over all SMs (one warp per read)
     while (warps > 1 && bp.st.cls_n[q] < (uint64_t)e->sms * warps) warps >>= 1;
@@ -1248,7 +1267,12 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
                   (size_t)a.warp_words * 4);
         return SNAP_E_INVAL;
     }
-    const FusedKernel kfn = team ? k_align_team : fused_kernel_for(Lmax);
+    // q-gram maps only when some read of the class can use the bound: for limit
+    // L the read length must lie in [9L - 7, L^2 / 8 - L]
+    bool qmaps = false;
+    for (int L = kQMinL; L <= Lmax && !qmaps; ++L)
+        qmaps = use_qfilter(std::min(mmax, L * L / 8 - L), L);
+    const FusedKernel kfn = team ? k_align_team : fused_kernel_for(Lmax, qmaps);
     const int threads = team ? kTeamWarps * 32 : warps * 32;
     if ((rc = raise_smem_limit((const void*)kfn, smem))) return rc;
     int per_sm = 0;
@@ -1275,7 +1299,7 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
         a.gcap = (uint32_t)gcap;
         plan->table_slots[q] = blocks * warps * gcap;
     }
-    if (Lmax >= kQMinL && mmax >= 2 * kQ) {
+    if (qmaps) {
         // presence maps start zero; kernels clear what they set before the next read
         DevBuf& gq = e->gqbits[q];
         void* before = gq.p;
@@ -1592,15 +1616,20 @@ extern "C" int snap_align_plain(const snap_index* idx, const uint8_t* reads,
     return align_host(idx, reads, offsets, n, p, out, true);
 }
 
-extern "C" int snap_index_configure(snap_index* idx, int autotune, int cuda_graphs) {
+extern "C" int snap_index_configure(snap_index* idx, int autotune, int cuda_graphs, int team) {
     clear_error();
     if (!idx) {
         set_error("snap_index_configure: index is NULL");
         return SNAP_E_INVAL;
     }
+    if (team < -1 || team > 1) {
+        set_error("snap_index_configure: team must be -1, 0 or 1 (got %d)", team);
+        return SNAP_E_INVAL;
+    }
     std::lock_guard<std::mutex> lock(idx->engine->mu);
     idx->engine->autotune = autotune != 0;
     idx->engine->use_graphs = cuda_graphs != 0;
+    idx->engine->team = team;
     if (!autotune) idx->engine->tuned.clear();
     return SNAP_OK;
 }

@@ -278,30 +278,29 @@ def test_c2_full_size_sampled(snap):
 
 
 def test_team_mode_equals_warp_mode(snap):
-    # Reads of 1.1-2 kb fall in one length class with limits up to 160.  A batch with
-    # fewer such reads than 8 per SM runs that class in team mode (a block per read,
-    # all warps on each edit distance); a batch of many runs one warp per read.
-    # Per-read results do not depend on the batch, so both must agree, and the oracle
-    # agrees on a sample.
-    import torch
+    # Reads of 2.5-4 kb fall in one length class with limits up to 320.  The same
+    # batch aligned with one warp per read (team=0), in team mode (team=1: a block
+    # per read, all its warps on each edit distance) and with the per-batch choice
+    # (team=-1) gives identical results, and the oracle agrees on a sample.
     w = synth.CONFIGS["C4"].scaled(G=3_000_000, n_reads=0)
     g, _ = w.make_genome()
     gi = snap.Index(g, w.seed_len)
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    n = 8 * sms + 200
-    lens = np.random.default_rng(7).integers(1100, 2001, n).astype(np.uint32)
+    n = 600
+    lens = np.random.default_rng(7).integers(2500, 4001, n).astype(np.uint32)
     rd = synth.reads(g, lens, w.sub_rate, w.indel_rate, w.indel_len, seed=17)
     dpr = w.max_dist_per_read(rd.lengths())
-    many = gi.align(rd.bases, rd.offsets, max_dist_per_read=dpr, **w.params())
-    assert gi.last_call_stats()["team_classes"] == 0
-    k = 300
-    sub = synth.reads(g, lens[:k], w.sub_rate, w.indel_rate, w.indel_len, seed=17)
-    assert np.array_equal(sub.bases, rd.bases[:int(rd.offsets[k])])
-    few = gi.align(sub.bases, sub.offsets, max_dist_per_read=dpr[:k], **w.params())
-    st = gi.last_call_stats()
-    assert st["team_classes"] == 1 and st["ed_filtered"] > 0
-    assert_same(few, many[:k], "team vs warp mode")
-    j = 60
-    ref, _ = oracle.Index(g, w.seed_len).align(sub.bases[:int(sub.offsets[j])], sub.offsets[:j + 1],
+    runs = {}
+    for team in (0, 1, -1):
+        gi.configure(team=team)
+        runs[team] = gi.align(rd.bases, rd.offsets, max_dist_per_read=dpr, **w.params())
+        st = gi.last_call_stats()
+        assert st["team_classes"] == (0 if team == 0 else 1), team
+        assert st["ed_filtered"] > 0
+    assert_same(runs[1], runs[0], "team vs warp mode")
+    assert_same(runs[-1], runs[0], "chosen vs warp mode")
+    with pytest.raises(snap.SnapError):
+        gi.configure(team=2)
+    j = 40
+    ref, _ = oracle.Index(g, w.seed_len).align(rd.bases[:int(rd.offsets[j])], rd.offsets[:j + 1],
                                                max_dist_per_read=dpr[:j], threads=4, **w.params())
-    assert_same(few[:j], ref, "team mode vs oracle")
+    assert_same(runs[1][:j], ref, "team mode vs oracle")
