@@ -319,7 +319,7 @@ def run_ours(args):
                 agg = dict(calls[-1])
                 for key in ("kernel_launches", "align_ms", "reads", "read_bases", "seeds",
                             "slot_reads", "list_entries", "ed_calls", "ed_over",
-                            "window_bytes"):
+                            "window_bytes", "ed_filtered", "probe_ms", "distance_ms"):
                     agg[key] = sum(c[key] for c in calls)
                 stats.append(agg)
             torch.cuda.synchronize()
@@ -348,15 +348,28 @@ def run_ours(args):
                  16 * st["slot_reads"] + 4 * st["list_entries"] + st["window_bytes"])
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (align_ms / 1e3) / 1e9
-    kname = "k_align_plain_stages" if plain else "k_align_fused"
+    kname = "plain_stages" if plain else "align_span"
     tr = _ncu_traffic(kname)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                 "traffic": None if tr is None else tr["dram_bytes_per_read"] * st["reads"],
-                "kernel": kname, "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel": ("k_plain_probe + k_plain_candidates + k_plain_distance + "
+                           "k_plain_replay" if plain else
+                           "k_align_light + k_split_classes + k_align_fused/k_align_team "
+                           "per length class"),
+                "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel_ms": align_ms,
                 "counters": {k: st[k] for k in ("seeds", "slot_reads", "list_entries",
-                                                "ed_calls", "ed_over", "window_bytes")}}
+                                                "ed_calls", "ed_over", "window_bytes",
+                                                "ed_filtered")}}
+    # the practical ceiling of this traffic: independent random reads of one
+    # aligned chunk (a 64-byte index bucket, a 32-byte sector)
+    try:
+        gc = {f"chunk{cb}_gbs": snap.measure_gather(8 << 30, cb, 1 << 28) for cb in (32, 64)}
+        gc["frac_of_chunk64"] = achieved / gc["chunk64_gbs"]
+        roofline["gather_ceiling"] = gc
+    except Exception as e:  # a measurement aid, not the product
+        roofline["gather_ceiling"] = {"error": str(e)[:200]}
 
     line = {
         "metric": METRIC, "value": value, "unit": "reads/s", "n_gpus": ws, "steps": args.steps,
@@ -388,6 +401,22 @@ def run_ours(args):
                              "ms_per_step": p_total * 1e3 / len(p_ms),
                              "gpu_launches_per_step": int(p_stats[-1]["kernel_launches"]),
                              "identical_results": bool(same)}
+            # the probe path alone: the plain form's seed-probe stage kernel, whose
+            # traffic is the packed s-mer (8 B) and seed record (16 B) per seed, the
+            # 16-byte index slots it reads, and per read its offsets and hit count
+            ps = p_stats[-1]
+            probe_ms = float(np.mean([q["probe_ms"] for q in p_stats]))
+            probe_bytes = 24 * ps["seeds"] + 16 * ps["slot_reads"] + 20 * ps["reads"]
+            if probe_ms > 0:
+                gbs = probe_bytes / (probe_ms / 1e3) / 1e9
+                line["probe_stage"] = {
+                    "kernel": "k_plain_probe", "algorithmic_bytes": probe_bytes,
+                    "kernel_ms": probe_ms, "achieved_gbs": gbs, "frac": gbs / peak,
+                    "probes": ps["seeds"], "slot_reads": ps["slot_reads"],
+                    "probes_per_s": ps["seeds"] / (probe_ms / 1e3)}
+                gc = roofline.get("gather_ceiling", {})
+                if "chunk64_gbs" in gc:
+                    line["probe_stage"]["frac_of_gather_chunk64"] = gbs / gc["chunk64_gbs"]
             line["batched_over_plain"] = line["value"] / line["plain"]["value"]
         except Exception as e:  # the plain form is a comparison, not the product
             line["plain"] = {"error": str(e)[:200]}

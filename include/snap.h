@@ -236,6 +236,10 @@ typedef struct {
                                  block, all warps of the block on each edit distance) */
     uint64_t ed_filtered;     /* edit distances (counted in ed_calls and ed_over) proven
                                  over the limit by the q-gram bound without the rounds */
+    double probe_ms;          /* plain form: the seed-probe stage kernel alone (its
+                                 traffic is seeds x (8 + 16) bytes + 16 per slot read);
+                                 0 for the batched form, where probes are fused */
+    double distance_ms;       /* plain form: the edit-distance stage kernel alone */
 } snap_call_stats;
 
 int snap_last_call_stats(const snap_index* index, snap_call_stats* out);
@@ -261,6 +265,21 @@ int snap_last_call_stats(const snap_index* index, snap_call_stats* out);
  * NULL index or team outside -1..1.
  */
 int snap_index_configure(snap_index* index, int autotune, int cuda_graphs, int team);
+
+/* Measurement helper; Algorithm 1 has no counterpart.  Every index probe,
+ * position-list read and genome-window fetch of the aligner reads a few dozen
+ * bytes at an unpredictable address, so the streaming-copy bandwidth of HBM
+ * overstates what that traffic can reach.  This measures the random-gather
+ * ceiling on the current device: about n_reads independent reads of one
+ * chunk_bytes-aligned chunk (16, 32 or 64 bytes) at pseudo-random chunk indices of a
+ * device buffer of buffer_bytes (>= 64 MiB; make it far larger than L2),
+ * 2048 threads per SM, chunk_bytes / 16 threads on each chunk and 4 chunks in
+ * flight per thread; best of three timed runs
+ * after one warm-up.  Writes the delivered chunk bytes per second / 1e9 to
+ * *gbs_out.  Allocates and frees the buffer itself; SNAP_E_NOMEM when it does
+ * not fit, SNAP_E_INVAL for other sizes. */
+int snap_measure_gather(uint64_t buffer_bytes, uint32_t chunk_bytes, uint64_t n_reads,
+                        double* gbs_out);
 
 /* Message for the last failed call on this thread ("" if none). */
 const char* snap_last_error(void);

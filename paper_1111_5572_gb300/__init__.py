@@ -28,6 +28,7 @@ EXPORTS = ("snap_index_build", "snap_index_free", "snap_index_info_get", "snap_a
            "snap_align_device", "snap_align_plain_device", "snap_align_plain",
            "snap_server_create", "snap_server_submit", "snap_server_wait", "snap_server_destroy",
            "snap_last_call_stats", "snap_align_device_noalloc", "snap_index_configure",
+           "snap_measure_gather",
            "snap_last_error")
 
 
@@ -60,7 +61,8 @@ class snap_call_stats(ctypes.Structure):
                 ("window_bytes", ctypes.c_uint64), ("light_threads", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("table_slots", ctypes.c_int32),
                 ("graph_replay", ctypes.c_int32), ("team_classes", ctypes.c_int32),
-                ("ed_filtered", ctypes.c_uint64)]
+                ("ed_filtered", ctypes.c_uint64), ("probe_ms", ctypes.c_double),
+                ("distance_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -91,6 +93,7 @@ def load_library(path: str = LIB_PATH):
     lib.snap_server_destroy.argtypes = [vp]
     lib.snap_last_call_stats.argtypes = [vp, P(snap_call_stats)]
     lib.snap_index_configure.argtypes = [vp, i32, i32, i32]
+    lib.snap_measure_gather.argtypes = [u64, ctypes.c_uint32, u64, P(ctypes.c_double)]
     lib.snap_last_error.argtypes = []
     lib.snap_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -114,6 +117,16 @@ def make_params(max_dist: int = 8, max_hits: int = 300, conf_diff: int = 2, num_
                 max_dist_per_read_ptr: Optional[int] = None) -> snap_params:
     return snap_params(int(max_dist), int(max_hits), int(conf_diff), int(num_seeds),
                        max_dist_per_read_ptr)
+
+
+def measure_gather(buffer_bytes: int = 8 << 30, chunk_bytes: int = 32,
+                   n_reads: int = 1 << 28) -> float:
+    """snap_measure_gather: GB/s delivered by independent random reads of one aligned
+    chunk each (the practical ceiling of index probes and window fetches)."""
+    out = ctypes.c_double()
+    _check(load_library().snap_measure_gather(int(buffer_bytes), int(chunk_bytes), int(n_reads),
+                                              ctypes.byref(out)), "snap_measure_gather")
+    return out.value
 
 
 class Index:

@@ -292,6 +292,8 @@ struct FusedArgs {
     // moved with 16-byte vector accesses
     int wx, wt, seed_cap, scap, lv_ints, warp_words;
     int off_xr, off_tw, off_seeds, off_tab, off_hits, off_dense, off_lv;
+    int off_par;  // parallel-drain scratch (par_words(par_mmax) words), 0 = none
+    int par_mmax;
 };
 
 struct WarpCounters {
@@ -331,7 +333,38 @@ struct WarpMem {
     uint32_t* gdense;
     uint32_t* qbits;  // q-gram bitmaps of the read, one per strand (or NULL: no filter)
     int* job;         // team mode: the lead warp's posted job (see k_align_team)
+    uint32_t* par;    // parallel-drain scratch, or NULL
 };
+
+// ---------------------------------------------------------------------------
+// Parallel drain.  Once the Baeza-Yates test passes, Algorithm 1 scores every
+// remaining candidate in pick order (most votes, then smaller key) with no
+// early return, and the votes no longer change, so the whole drain order is
+// known up front.  The warp ranks the unscored candidates once, then takes them
+// 32 at a time: each lane computes one candidate's distance at a bound Lc with
+// its own Landau-Vishkin (lv_lane), and the warp replays the 32 in order, each
+// at the limit Algorithm 1 would use for it.  Every limit is d_best + c - 1,
+// d_best - 1 or (d_best > d_max) d_max + c - 1, and d_best never grows, so
+// Lc = min(d_best, d_max) + c - 1 bounds all later limits (a limit itself can
+// grow: a new best in the old best's 32-base bucket can lift d_second clear of
+// it).  A distance d0 found at Lc gives the one at L <= Lc as
+// (d0 <= L ? d0 : over): the results are those of scoring one by one.
+// ---------------------------------------------------------------------------
+constexpr int kParMaxL = 7;                     // lane diagonals: 2 * 7 + 3 = 17
+constexpr int kParMaxCands = 128;               // unscored candidates ranked at once
+// scratch words per warp for reads up to mmax bases: the ranked keys, later the
+// lanes' genome windows (column layout), then the slots in drain order and the
+// lanes' diagonals
+__host__ __device__ constexpr int par_window_words(int mmax) {
+    return (15 + mmax + kParMaxL + 15) / 16 + 2;
+}
+__host__ __device__ constexpr int par_union_words(int mmax) {
+    return 2 * kParMaxCands > 32 * par_window_words(mmax) ? 2 * kParMaxCands
+                                                           : 32 * par_window_words(mmax);
+}
+__host__ __device__ constexpr int par_words(int mmax) {
+    return par_union_words(mmax) + kParMaxCands + 32 * (2 * kParMaxL + 3);
+}
 
 // ---------------------------------------------------------------------------
 // q-gram rejection ahead of large-limit edit distances (the q-gram lemma).  If some prefix Y of
@@ -684,8 +717,9 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
             if (lane == 0) atomicOr(a.status, kStTableFull);
         }
         if (ok) {
-            int nd = 0;      // distinct candidates so far (slots listed in dense)
-            int qbuilt = 0;  // strands whose q-gram bitmap is built for this read
+            int nd = 0;        // distinct candidates so far (slots listed in dense)
+            int qbuilt = 0;    // strands whose q-gram bitmap is built for this read
+            int par_skip = 0;  // drain iterations before the parallel drain is retried
             int d_best = kInf, d_second = kInf, nh = 0, t = 0;
             unsigned long long best_key = 0;
             bool any_nonpopular = false, returned = false;
@@ -695,11 +729,8 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                 if (d_second >= d_best + c) return d_best + c - 1;
                 return d_best - 1;
             };
-            auto score = [&](unsigned long long packed) {
-                const uint32_t slot = (uint32_t)(packed & 0xfffffu);
-                const unsigned long long key = kKeyMask - ((packed >> 20) & kKeyMask);
-                const int L = limit();
-                const int d = candidate_distance<LVD, TEAM>(a, wm, m, key, L, lane, wc, qbuilt);
+            // the bookkeeping of one scored candidate (warp-uniform arguments)
+            auto record = [&](uint32_t slot, unsigned long long key, int d) {
                 if (lane == 0) {
                     tab[slot].state = d >= 0 ? d : kOver;
                     if (d >= 0) {
@@ -728,6 +759,95 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                     }
                 }
             };
+            auto score = [&](unsigned long long packed) {
+                const uint32_t slot = (uint32_t)(packed & 0xfffffu);
+                const unsigned long long key = kKeyMask - ((packed >> 20) & kKeyMask);
+                const int L = limit();
+                const int d = candidate_distance<LVD, TEAM>(a, wm, m, key, L, lane, wc, qbuilt);
+                record(slot, key, d);
+            };
+            // the whole drain, in parallel (see par_words); false when it does not
+            // apply (limit above kParMaxL or too many candidates) and nothing was done
+            auto drain_parallel = [&]() -> bool {
+                if (min(d_best, dmax) + c - 1 > kParMaxL) return false;
+                unsigned long long* upk = reinterpret_cast<unsigned long long*>(wm.par);
+                uint32_t* Tp = wm.par;  // after ranking: the lanes' windows
+                uint32_t* order = wm.par + par_union_words(a.par_mmax);
+                int* Rp = reinterpret_cast<int*>(order + kParMaxCands);
+                // unscored candidates, packed as in table_pick (distinct keys)
+                int U = 0;
+                for (int j0 = 0; j0 < nd; j0 += 32) {
+                    const int j = j0 + lane;
+                    unsigned long long pk = 0;
+                    if (j < nd) {
+                        const uint32_t slot = dense[j];
+                        const CandSlot cs = tab[slot];
+                        if (cs.state == kUnscored)
+                            pk = ((unsigned long long)cs.votes << 53) |
+                                 ((kKeyMask - cs.key) << 20) | (unsigned long long)slot;
+                    }
+                    const unsigned b = __ballot_sync(kFull, pk != 0);
+                    const int pos = U + __popc(b & ((1u << lane) - 1));
+                    if (pk && pos < kParMaxCands) upk[pos] = pk;
+                    U += __popc(b);
+                }
+                if (U > kParMaxCands) {
+                    par_skip = U - kParMaxCands;  // sequential picks until few enough are left
+                    return false;
+                }
+                __syncwarp();
+                // drain order: entry e goes to position #{i : upk[i] > upk[e]}
+                for (int e = lane; e < U; e += 32) {
+                    const unsigned long long mine = upk[e];
+                    int rank = 0;
+                    for (int i = 0; i < U; ++i) rank += (upk[i] > mine);
+                    order[rank] = (uint32_t)(mine & 0xfffffu);
+                }
+                __syncwarp();  // upk is reused for the windows
+                // chunks of 32 in pick order
+                for (int c0 = 0; c0 < U; c0 += 32) {
+                    const int k = min(32, U - c0);
+                    const uint32_t* chunk = order + c0;
+                    const int Lc = min(d_best, dmax) + c - 1;  // bounds every later limit
+                    int d0 = kOver;
+                    unsigned words = 0;
+                    unsigned long long my_key = 0;
+                    if (lane < k) {
+                        my_key = tab[chunk[lane]].key;
+                        if (Lc >= 0) {
+                            const uint64_t p = my_key >> 1;
+                            const int n_t = (int)min(a.G - p, (uint64_t)(m + Lc));
+                            const int tb = (int)(p & 15);
+                            const int nwt = (tb + n_t + 15) / 16 + 2;
+                            if (nwt <= par_window_words(a.par_mmax)) {
+                                const uint32_t* gw = a.genome + (p >> 4);
+                                for (int w = 0; w < nwt; ++w) Tp[w * 32 + lane] = __ldg(gw + w);
+                                words = (unsigned)nwt;
+                                d0 = lv_lane((my_key & 1) ? wm.Xr : wm.Xf, 1, m, Tp + lane, 32, tb,
+                                             n_t, Lc, Rp + lane, 32);
+                            } else {
+                                atomicOr(a.status, kStInternal);  // cannot happen: layout bug
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) words += __shfl_xor_sync(kFull, words, o);
+                    if (lane == 0) wc.window_words += words;
+                    for (int j = 0; j < k; ++j) {
+                        const uint32_t slot = chunk[j];
+                        const unsigned long long key = __shfl_sync(kFull, my_key, j);
+                        const int dj = __shfl_sync(kFull, d0, j);
+                        const int L = limit();
+                        const int d = (L >= 0 && dj >= 0 && dj <= L) ? dj : kOver;
+                        if (L >= 0 && lane == 0) {
+                            wc.ed_calls++;
+                            wc.ed_over += (d < 0);
+                        }
+                        record(slot, key, d);
+                    }
+                }
+                return true;
+            };
 
             // One pass per non-popular seed: add its votes, pick and score one
             // candidate, test the exits.  Once the Baeza-Yates test passes the loop
@@ -735,6 +855,12 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
             bool draining = false;
             int i = 0;
             for (;;) {
+                if constexpr (LVD > 0 && !TEAM) {
+                    if (draining && wm.par) {
+                        if (par_skip == 0 && drain_parallel()) break;
+                        par_skip = max(0, par_skip - 1);
+                    }
+                }
                 SeedRec rec;
                 if (!draining) {
                     while (i < n && (wm.seeds[i].flags & kSeedPopular)) ++i;
@@ -838,6 +964,7 @@ __global__ void __launch_bounds__(256, 4) k_align_fused(FusedArgs a) {
     wm.ghits = a.ghits ? a.ghits + gw * (a.gcap / 2) : nullptr;
     wm.gdense = a.gdense ? a.gdense + gw * (a.gcap / 2) : nullptr;
     wm.qbits = a.gqbits ? a.gqbits + gw * (2 * kQWords) : nullptr;
+    wm.par = a.off_par ? base + a.off_par : nullptr;
     for (int j = lane; j < a.scap; j += 32) wm.stab[j] = empty_slot();
     __syncwarp();
     WarpCounters wc;
@@ -875,6 +1002,7 @@ __global__ void __launch_bounds__(kTeamWarps * 32) k_align_team(FusedArgs a) {
     wm.gdense = a.gdense ? a.gdense + gw * (a.gcap / 2) : nullptr;
     wm.qbits = a.gqbits ? a.gqbits + gw * (2 * kQWords) : nullptr;
     wm.job = reinterpret_cast<int*>(smem + a.warp_words);
+    wm.par = nullptr;
     if (wib != 0) {
         team_helper(a, wm);
         return;
@@ -1172,6 +1300,13 @@ static int finish_status(Engine* e, cudaStream_t stream, const char* where, uint
     L.table_slots = e->last_shape.scap;
     L.graph_replay = e->last_graph;
     L.team_classes = e->last_team;
+    L.probe_ms = L.distance_ms = 0;
+    if (e->last_plain) {
+        cudaEventElapsedTime(&ms, e->pev[3], e->pev[0]);
+        L.probe_ms = ms;
+        cudaEventElapsedTime(&ms, e->pev[1], e->pev[2]);
+        L.distance_ms = ms;
+    }
     return SNAP_OK;
 }
 
@@ -1235,13 +1370,14 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     // many seeds (long reads): seed records in global memory, more warps per SM
     const bool seeds_global = nmax > 64;
     const int seed_words = seeds_global ? 0 : 4 * a.seed_cap;
-    const int fixed_words = 2 * a.wx + a.wt + seed_words + a.lv_ints;
-    const int budget_words = 200 * 1024 / 4;  // per block; 7 words per table slot
-    // a class of large limits with too few reads to give each SM several warps
-    // runs in team mode (a block per read); `warps` counts the per-read warps
-    // (lead warps) of a block, which own the per-warp layout below
     const uint64_t team_below = (uint64_t)e->sms * std::max(kTeamReadsPerSm, mmax / 12);
     const bool team = Lmax > 31 && (e->team < 0 ? bp.st.cls_n[q] < team_below : e->team == 1);
+    const int pwords = (Lmax <= 31 && !team) ? par_words(mmax) : 0;  // register-diagonal kernels
+    const int fixed_words = 2 * a.wx + a.wt + seed_words + a.lv_ints + pwords;
+    const int budget_words = 200 * 1024 / 4;  // per block; 7 words per table slot
+    // a class of large limits with too few reads to give each SM several warps
+    // runs in team mode (a block per read, `team` above); `warps` counts the
+    // per-read warps (lead warps) of a block, which own the per-warp layout below
     int warps = team ? 1 : std::max(1, shape.warps);
     // a class with few reads spreads them over all SMs (one warp per read)
     while (warps > 1 && bp.st.cls_n[q] < (uint64_t)e->sms * warps) warps >>= 1;
@@ -1256,8 +1392,11 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     a.off_hits = a.off_tab + 4 * scap;            // CandSlot: 4 words
     a.off_dense = a.off_hits + 4 * (scap / 2);    // HitRec: 4 words, scap/2 of them
     a.off_lv = a.off_dense + up4(scap / 2);       // dense slot list: scap/2 words
-    a.warp_words = a.off_lv + a.lv_ints;
-    if ((a.off_seeds | a.off_tab | a.off_hits | a.off_dense | a.off_lv | a.warp_words) & 3) {
+    a.off_par = pwords ? a.off_lv + a.lv_ints : 0;
+    a.par_mmax = mmax;
+    a.warp_words = a.off_lv + a.lv_ints + pwords;
+    if ((a.off_seeds | a.off_tab | a.off_hits | a.off_dense | a.off_lv | a.off_par |
+         a.warp_words) & 3) {
         set_error("snap_align: internal shared-memory layout is not 16-byte aligned");
         return SNAP_E_INTERNAL;
     }
@@ -1544,6 +1683,7 @@ int align_batch_device(const snap_index* idx, Engine* e, const uint8_t* d_reads,
     e->last_shape = LaunchShape{0, 0, 0};  // set again by the batched form
     e->last_graph = 0;
     e->last_team = 0;
+    e->last_plain = plain;
     BatchPrep bp;
     if ((rc = prepare_batch(idx, e, d_reads, d_offsets, n, p, stream, &bp, where))) return rc;
     rc = plain ? align_plain(idx, e, d_offsets, n, p, d_out, stream, bp)

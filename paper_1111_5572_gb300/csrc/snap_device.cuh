@@ -193,6 +193,58 @@ __device__ __forceinline__ int slide(const uint32_t* X, int m, const uint32_t* T
     }
 }
 
+// 16 bases starting at base i of a packed sequence whose word w sits at w * stride.
+__device__ __forceinline__ uint32_t get16s(const uint32_t* w, int i, int stride) {
+    const int q = i >> 4;
+    return __funnelshift_r(w[q * stride], w[(q + 1) * stride], (uint32_t)(i & 15) * 2u);
+}
+
+// The same distance computed by one thread: rounds e = 0..L, diagonals k = -e..e
+// in increasing order, updated in place in R (2L+3 ints at stride rs; round
+// e-1's value is only read for |k| <= e-1, so R needs no initialisation).  X and
+// T are packed at word strides xs and ts.
+__device__ __forceinline__ int lv_lane(const uint32_t* X, int xs, int m, const uint32_t* Tw, int ts,
+                                       int tb, int n, int L, int* R, int rs) {
+    constexpr int NEG = -0x40000000;
+    if (L < 0) return kOver;
+    for (int e = 0; e <= L; ++e) {
+        int left_old = NEG;
+        for (int k = -e; k <= e; ++k) {
+            int* slot = R + (k + L + 1) * rs;
+            const int cur_old = (k >= -(e - 1) && k <= e - 1) ? *slot : NEG;
+            int r;
+            if (e == 0) {
+                r = 0;
+            } else {
+                const int right_old = (k + 1 <= e - 1) ? slot[rs] : NEG;
+                r = max(max(cur_old + 1, right_old + 1), left_old);
+            }
+            left_old = cur_old;
+            if (r > m) r = m;
+            if (r + k > n) r = n - k;
+            if (r < 0 || r + k < 0) {
+                *slot = NEG;
+                continue;
+            }
+            for (;;) {
+                const int lim = min(m - r, n - (r + k));
+                if (lim <= 0) break;
+                const uint32_t x = get16s(X, r, xs) ^ get16s(Tw, tb + r + k, ts);
+                const int adv = x ? ((__ffs(x) - 1) >> 1) : 16;
+                if (adv >= lim) {
+                    r += lim;
+                    break;
+                }
+                r += adv;
+                if (adv < 16) break;
+            }
+            *slot = r;
+            if (r >= m) return e;
+        }
+    }
+    return kOver;
+}
+
 template <int D>
 __device__ inline int lv_warp_reg(const uint32_t* X, int m, const uint32_t* Tw, int tb, int n, int L,
                            int lane) {

@@ -51,6 +51,7 @@ struct Engine {
     int last_graph = 0;
     int last_team = 0;  // classes of the last batch that ran in team mode
     int team = -1;      // team mode: -1 chosen per batch, 0 never, 1 always
+    bool last_plain = false;  // the last call ran the plain form (pev marks are valid)
     uint64_t overflow_budget = 4ull << 30;  // device bytes for per-warp global candidate tables
     // plain-form workspace
     DevBuf p_seeds, p_hits, p_hitoff, p_partial, p_table, p_events, p_hitlist, p_items, p_misc,

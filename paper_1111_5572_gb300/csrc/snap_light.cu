@@ -58,62 +58,12 @@ struct LightArgs {
     DevCounters* ctr;
 };
 
-// 16 / 32 bases from a column-stored packed sequence (stride = threads per block)
-__device__ __forceinline__ uint32_t col16(const uint32_t* col, int i, int st) {
-    const int q = i >> 4;
-    return __funnelshift_r(col[q * st], col[(q + 1) * st], (uint32_t)(i & 15) * 2u);
-}
+// 32 bases from a column-stored packed sequence (stride = threads per block)
 __device__ __forceinline__ uint64_t col32(const uint32_t* col, int i, int st) {
     const int q = i >> 4;
     const uint32_t sh = (uint32_t)(i & 15) * 2u;
     const uint32_t w0 = col[q * st], w1 = col[(q + 1) * st], w2 = col[(q + 2) * st];
     return ((uint64_t)__funnelshift_r(w1, w2, sh) << 32) | __funnelshift_r(w0, w1, sh);
-}
-
-// Farthest reach per diagonal by one thread: rounds e = 0..L, diagonals k = -e..e
-// in increasing order updated in place (the old value of k-1 is carried).
-__device__ __forceinline__ int lv_thread(const uint32_t* X, int m, const uint32_t* Tw, int tb,
-                                         int n, int L, int* R, int st) {
-    constexpr int NEG = -0x40000000;
-    if (L < 0) return kOver;
-    // R[k] holds round e-1's value only for |k| <= e-1; anything outside that
-    // range is read as "unreachable", so the array needs no initialisation
-    for (int e = 0; e <= L; ++e) {
-        int left_old = NEG;
-        for (int k = -e; k <= e; ++k) {
-            int* slot = R + (k + L + 1) * st;
-            const int cur_old = (k >= -(e - 1) && k <= e - 1) ? *slot : NEG;
-            int r;
-            if (e == 0) {
-                r = 0;
-            } else {
-                const int right_old = (k + 1 <= e - 1) ? slot[st] : NEG;
-                r = max(max(cur_old + 1, right_old + 1), left_old);
-            }
-            left_old = cur_old;
-            if (r > m) r = m;
-            if (r + k > n) r = n - k;
-            if (r < 0 || r + k < 0) {
-                *slot = NEG;
-                continue;
-            }
-            for (;;) {
-                const int lim = min(m - r, n - (r + k));
-                if (lim <= 0) break;
-                const uint32_t x = col16(X, r, st) ^ col16(Tw, tb + r + k, st);
-                const int adv = x ? ((__ffs(x) - 1) >> 1) : 16;
-                if (adv >= lim) {
-                    r += lim;
-                    break;
-                }
-                r += adv;
-                if (adv < 16) break;
-            }
-            *slot = r;
-            if (r >= m) return e;
-        }
-    }
-    return kOver;
 }
 
 __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
@@ -258,7 +208,7 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                             const int nwt = (tb + n_t + 15) / 16 + 2;
                             for (int w = 0; w < nwt; ++w) Tw[w * st] = __ldg(a.genome + w0 + w);
                             c_words += nwt;
-                            d = lv_thread((key & 1) ? Xr : Xf, m, Tw, tb, n_t, L, R, st);
+                            d = lv_lane((key & 1) ? Xr : Xf, st, m, Tw, st, tb, n_t, L, R, st);
                         }
                         ++c_ed;
                         c_over += (d < 0);

@@ -452,6 +452,7 @@ int align_plain(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uin
     a.n_items = misc;  // [0] item count, [1] hit total
     SNAP_CUDA(cudaMemsetAsync(a.hits_per_read, 0, n * sizeof(uint32_t), stream), "clear");
     SNAP_CUDA(cudaMemsetAsync(misc, 0, 64, stream), "clear");
+    SNAP_CUDA(cudaEventRecord(e->pev[3], stream), "event");
     e->launches++;
     k_plain_probe<<<grid_cap(e->sms, nseed, 256), 256, 0, stream>>>(a);
     SNAP_CUDA(cudaGetLastError(), "probe launch");

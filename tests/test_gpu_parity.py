@@ -66,6 +66,19 @@ def test_c2_repeat_rich_scaled(snap, G, n, plain):
     assert st.n_multiple > 0  # the repeat families exercise the multiple-hit paths
 
 
+def test_c5_repeat_dense_scaled(snap):
+    # C5 recipe (50% of the genome in repeat families) on 10 Mbp: reads with dozens of
+    # candidates, scored mostly in the drain, where the warp kernel ranks them and
+    # scores 32 at a time (the limit can grow there: a new best in the old best's
+    # 32-base bucket can lift d_second clear of it)
+    w = synth.CONFIGS["C5"].scaled(G=10_000_000, n_reads=60_000)
+    g, _ = w.make_genome()
+    rd = w.make_reads(g)
+    got, ref, st = _run_both(snap, g, rd, w)
+    assert_same(got, ref, "C5 scaled")
+    assert st.n_multiple > 1000
+
+
 @pytest.mark.parametrize("plain", [False, True])
 def test_c3_uneven_lengths_scaled(snap, plain):
     w = synth.CONFIGS["C3"].scaled(G=4_000_000, n_reads=4000)
