@@ -6,9 +6,10 @@
 // most 16 index positions; the thread then runs the whole per-read loop alone:
 // seed probes, votes in a small per-thread candidate list, the most-voted pick,
 // the limit schedule, a Landau-Vishkin edit distance over one diagonal at a time,
-// best / second best over 32-base buckets and the exits.  Any other read is
-// appended to a device list that the warp-per-read kernel (snap_align.cu) drains
-// next, so every read is aligned by exactly one of the two, with the same
+// best / second best over 32-base buckets and the exits.  Any other read, and
+// any read whose edit distances would need a fifth round, is appended to a
+// device list that the warp-per-read kernel (snap_align.cu) drains next (from
+// scratch), so every result comes from exactly one of the two, with the same
 // readings of the paper (see snap_align.cu).
 //
 // Per-thread arrays live in shared memory in column order (word w of thread t at
@@ -27,6 +28,10 @@ constexpr int kLightMaxM = kLightBucketMaxM;
 constexpr int kLightMaxSeeds = kLightBucketMaxSeeds;
 constexpr int kLightMaxL = kLightBucketMaxL;
 constexpr int kLightMaxCands = 16;
+// A thread gives its read to the warp-per-read kernel rather than start edit
+// distance round 4 (16 diagonals done): the rare long distances would otherwise
+// hold the other 31 lanes of the warp idle.
+constexpr int kLightMaxRounds = 4;
 constexpr int kLightXW = kLightMaxM / 16 + 2;                           // read words + 2
 constexpr int kLightTW = (15 + kLightMaxM + kLightMaxL + 15) / 16 + 2;  // window words
 constexpr int kLightRW = 2 * kLightMaxL + 3;                            // diagonals + 2
@@ -145,6 +150,7 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                 int d_best = kInfL, d_second = kInfL;
                 unsigned long long best_key = 0;
                 bool any_nonpopular = false, returned = false, draining = false;
+                bool gave_up = false;
                 int i = 0;
                 for (;;) {
                     if (!draining) {
@@ -208,7 +214,12 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                             const int nwt = (tb + n_t + 15) / 16 + 2;
                             for (int w = 0; w < nwt; ++w) Tw[w * st] = __ldg(a.genome + w0 + w);
                             c_words += nwt;
-                            d = lv_lane((key & 1) ? Xr : Xf, st, m, Tw, st, tb, n_t, L, R, st);
+                            d = lv_lane((key & 1) ? Xr : Xf, st, m, Tw, st, tb, n_t, L, R, st,
+                                        kLightMaxRounds);
+                            if (d == kLaneGaveUp) {
+                                gave_up = true;  // the warp-per-read kernel redoes this read
+                                break;
+                            }
                         }
                         ++c_ed;
                         c_over += (d < 0);
@@ -242,7 +253,9 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                         if (t >= d_best + c) draining = true;
                     }
                 }
-                if (!returned && d_best <= dmax && d_second >= d_best + c) {
+                if (gave_up) {
+                    heavy = true;
+                } else if (!returned && d_best <= dmax && d_second >= d_best + c) {
                     res_cls = SNAP_SINGLE_HIT;
                 } else if (returned || d_best <= dmax || !any_nonpopular) {
                     res_cls = SNAP_MULTIPLE_HITS;
