@@ -50,6 +50,9 @@ def _args():
     ap.add_argument("--workload", default="C2")
     ap.add_argument("--form", choices=["batched", "plain"], default="batched")
     ap.add_argument("--reads", type=int, default=0, help="override reads per step")
+    ap.add_argument("--genome-bp", type=int, default=0,
+                    help="scale the workload's genome to this many bases (same recipe), for "
+                         "profiling a kernel on a small case")
     ap.add_argument("--batch", type=int, default=4_000_000,
                     help="reads per align call; a step aligns all the workload's reads")
     ap.add_argument("--serve", action="store_true",
@@ -171,6 +174,10 @@ def make_workload(args, rank: int):
     import synth
     w = synth.CONFIGS[args.workload]
     n = args.reads or w.n_reads
+    if n <= 0:
+        raise SystemExit(f"{args.workload} is a serving recipe: give --reads (or use --serve)")
+    if args.genome_bp:
+        w = w.scaled(G=args.genome_bp, n_reads=n)
     t0 = time.perf_counter()
     g, _ = w.make_genome()
     rd = w.make_reads(g, n=n, first_index=rank * n)
@@ -363,13 +370,17 @@ def run_ours(args):
                                                 "ed_calls", "ed_over", "window_bytes",
                                                 "ed_filtered")}}
     # the practical ceiling of this traffic: independent random reads of one
-    # aligned chunk (a 64-byte index bucket, a 32-byte sector)
-    try:
-        gc = {f"chunk{cb}_gbs": snap.measure_gather(8 << 30, cb, 1 << 28) for cb in (32, 64)}
-        gc["frac_of_chunk64"] = achieved / gc["chunk64_gbs"]
-        roofline["gather_ceiling"] = gc
-    except Exception as e:  # a measurement aid, not the product
-        roofline["gather_ceiling"] = {"error": str(e)[:200]}
+    # aligned chunk (a 64-byte index bucket, a 32-byte sector); not under
+    # --profile, whose launch list should hold the aligner's kernels only
+    roofline["gather_ceiling"] = None
+    if not args.profile:
+        try:
+            gc = {f"chunk{cb}_gbs": snap.measure_gather(8 << 30, cb, 1 << 28)
+                  for cb in (32, 64)}
+            gc["frac_of_chunk64"] = achieved / gc["chunk64_gbs"]
+            roofline["gather_ceiling"] = gc
+        except Exception as e:  # a measurement aid, not the product
+            roofline["gather_ceiling"] = {"error": str(e)[:200]}
 
     line = {
         "metric": METRIC, "value": value, "unit": "reads/s", "n_gpus": ws, "steps": args.steps,
@@ -386,7 +397,7 @@ def run_ours(args):
         "input_gen_s": gen_s, "wall_s_timed": wall,
         "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
         "launch_shape": {k: st[k] for k in ("light_threads", "warps_per_block", "table_slots",
-                                            "graph_replay")},
+                                            "graph_replay", "team_classes")},
     }
 
     # the plain one-launch-per-stage form on the same GPU and inputs

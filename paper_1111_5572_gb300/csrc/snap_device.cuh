@@ -200,21 +200,23 @@ __device__ __forceinline__ uint32_t get16s(const uint32_t* w, int i, int stride)
 }
 
 // The same distance computed by one thread: rounds e = 0..L, diagonals k = -e..e
-// in increasing order, updated in place in R (2L+3 ints at stride rs; round
-// e-1's value is only read for |k| <= e-1, so R needs no initialisation).  X and
-// T are packed at word strides xs and ts.  Returns kLaneGaveUp instead of
-// starting round max_rounds (a caller that hands costly reads elsewhere).
+// in increasing order, updated in place in R (round e-1's value is only read for
+// |k| <= e-1, so R needs no initialisation).  X and T are packed at word strides
+// xs and ts.  Returns kLaneGaveUp instead of starting round max_rounds (a caller
+// that hands costly reads elsewhere); R holds 2 min(L, max_rounds - 1) + 3 ints
+// at stride rs.
 constexpr int kLaneGaveUp = -3;
 __device__ __forceinline__ int lv_lane(const uint32_t* X, int xs, int m, const uint32_t* Tw, int ts,
                                        int tb, int n, int L, int* R, int rs,
                                        int max_rounds = 0x7fffffff) {
     constexpr int NEG = -0x40000000;
     if (L < 0) return kOver;
+    const int off = min(L, max_rounds - 1) + 1;  // R index of diagonal k is k + off
     for (int e = 0; e <= L; ++e) {
         if (e >= max_rounds) return kLaneGaveUp;
         int left_old = NEG;
         for (int k = -e; k <= e; ++k) {
-            int* slot = R + (k + L + 1) * rs;
+            int* slot = R + (k + off) * rs;
             const int cur_old = (k >= -(e - 1) && k <= e - 1) ? *slot : NEG;
             int r;
             if (e == 0) {

@@ -34,7 +34,7 @@ constexpr int kLightMaxCands = 16;
 constexpr int kLightMaxRounds = 4;
 constexpr int kLightXW = kLightMaxM / 16 + 2;                           // read words + 2
 constexpr int kLightTW = (15 + kLightMaxM + kLightMaxL + 15) / 16 + 2;  // window words
-constexpr int kLightRW = 2 * kLightMaxL + 3;                            // diagonals + 2
+constexpr int kLightRW = 2 * (kLightMaxRounds - 1) + 3;                 // diagonals + 2
 constexpr int kLightWords = 2 * kLightXW + kLightTW + kLightRW;
 
 namespace {
