@@ -156,14 +156,16 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, if taken on these sources."""
+def _ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per read from a committed ncu summary, if taken on these kernel
+    sources and this workload."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         ent = d.get(kernel)
-        if ent and ent.get("source_hash") == _kernel_source_hash():
+        if (ent and ent.get("source_hash") == _kernel_source_hash() and
+                ent.get("workload") == workload):
             return ent
     except Exception:
         pass
@@ -356,7 +358,7 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     achieved = alg_bytes / (align_ms / 1e3) / 1e9
     kname = "plain_stages" if plain else "align_span"
-    tr = _ncu_traffic(kname)
+    tr = _ncu_traffic(kname, w.name)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                 "traffic": None if tr is None else tr["dram_bytes_per_read"] * st["reads"],
