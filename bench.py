@@ -63,6 +63,9 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--sweep-hmax", default="",
+                    help="comma-separated h_max values: for each, reads/s of the batched form "
+                         "and accuracy against the generator's truth (aligned %%, error %%)")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up plus the timed steps only (no plain form, e2e or CPU "
                          "baseline): the command to run under ncu")
@@ -546,12 +549,104 @@ def run_serve(args):
     return 0
 
 
+# A confident alignment is correct when it is on the read's true strand and within
+# this many bases of its true start (the configs' longest indel is 20 bases).
+CORRECT_WINDOW = 20
+
+
+def accuracy(got, rd) -> dict:
+    """Aligned % (single-hit class: the paper's confidently mapped reads) and error %
+    (confident reads on the wrong strand or more than CORRECT_WINDOW bases away)."""
+    cls = got["cls"].astype(np.int64)
+    single = cls == 1
+    ok = single & (got["strand"].astype(np.int64) == rd.strand.astype(np.int64)) & \
+        (np.abs(got["location"].astype(np.int64) - rd.origin) <= CORRECT_WINDOW)
+    ns = int(single.sum())
+    return {"aligned_pct": 100.0 * ns / len(cls),
+            "error_pct": 100.0 * (ns - int(ok.sum())) / max(1, ns),
+            "multiple_pct": 100.0 * float((cls == 2).mean()),
+            "not_found_pct": 100.0 * float((cls == 0).mean())}
+
+
+def run_sweep_hmax(args):
+    """h_max sweep (Ongoing Work, Observations: accuracy grows with h_max, throughput
+    falls): for each h_max, device-resident reads/s of the batched form over the
+    workload's reads, accuracy against the generator's truth, and a parity sample
+    against the oracle."""
+    import torch
+
+    import oracle
+    import paper_1111_5572_gb300 as snap
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w, g, rd, dpr, gen_s = make_workload(args, 0)
+    n = rd.n
+    idx = snap.Index(g, w.seed_len)
+    d_b = torch.from_numpy(rd.bases).to(dev)
+    d_o = torch.from_numpy(rd.offsets.view(np.int64)).to(dev)
+    d_out = torch.zeros((n, 16), dtype=torch.uint8, device=dev)
+    d_dpr = None if dpr is None else torch.from_numpy(dpr).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    batch = max(1, min(args.batch, n))
+    sample = rd.subset(np.arange(min(n, 20_000)))
+    restricted = w.G > 500_000_000
+    oidx = oracle.Index(g, w.seed_len, kmer_filter=oracle.read_seed_kmers(
+        sample.bases, sample.offsets, w.seed_len, w.num_seeds) if restricted else None)
+    points = []
+    with ClockSampler(0) as clk:
+        for h in [int(x) for x in args.sweep_hmax.split(",") if x.strip()]:
+            params = dict(w.params(), max_hits=h)
+
+            def step():
+                for b0 in range(0, n, batch):
+                    m_ = min(batch, n - b0)
+                    idx.align_device(d_b, d_o[b0:b0 + m_ + 1], d_out[b0:b0 + m_],
+                                     d_max_dist_per_read=None if d_dpr is None
+                                     else d_dpr[b0:b0 + m_], stream=stream, **params)
+
+            for _ in range(max(3, args.warmup)):
+                step()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            got = d_out.cpu().numpy().view(snap.RESULT_DTYPE).reshape(-1)
+            ref, _ = oidx.align(sample.bases, sample.offsets,
+                                max_dist_per_read=None if dpr is None else dpr[:sample.n],
+                                threads=os.cpu_count() or 1, **params)
+            mism = sum(int((got[f][:sample.n] != ref[f]).sum())
+                       for f in ("location", "edit_distance", "strand", "cls"))
+            points.append({"h_max": h, "reads_per_s": n * len(ms) / (sum(ms) / 1e3),
+                           "ms_per_step": sum(ms) / len(ms), **accuracy(got, rd),
+                           "parity_sample": {"reads": sample.n, "field_mismatches": mism}})
+    line = {"metric": METRIC, "mode": "sweep_hmax", "unit": "reads/s", "n_gpus": 1,
+            "dtype": "u8", "data": "synthetic",
+            "config": {"workload": w.name, "genome_bp": w.G, "reads": n,
+                       "correct_window_bases": CORRECT_WINDOW, "steps": args.steps,
+                       "l2": "flushed between steps (512 MiB write)"},
+            "points": points, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.sweep_hmax:
+        return run_sweep_hmax(args)
     return run_ours(args)
 
 

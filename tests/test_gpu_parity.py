@@ -79,6 +79,19 @@ def test_c5_repeat_dense_scaled(snap):
     assert st.n_multiple > 1000
 
 
+@pytest.mark.parametrize("h_max", [30, 3000])
+def test_hmax_sweep_points(snap, h_max):
+    # the h_max sweep's end points on the repeat-dense recipe (seeds hitting 30-3000
+    # places: popular seeds, long vote lists, many candidates per read)
+    w = replace(synth.CONFIGS["C5"].scaled(G=10_000_000, n_reads=20_000), max_hits=h_max)
+    g, _ = w.make_genome()
+    rd = w.make_reads(g)
+    got, ref, st = _run_both(snap, g, rd, w)
+    assert_same(got, ref, f"C5 scaled h_max={h_max}")
+    if h_max == 30:
+        assert st.seeds_popular > 0
+
+
 @pytest.mark.parametrize("plain", [False, True])
 def test_c3_uneven_lengths_scaled(snap, plain):
     w = synth.CONFIGS["C3"].scaled(G=4_000_000, n_reads=4000)
