@@ -66,6 +66,9 @@ def _args():
     ap.add_argument("--sweep-hmax", default="",
                     help="comma-separated h_max values: for each, reads/s of the batched form "
                          "and accuracy against the generator's truth (aligned %%, error %%)")
+    ap.add_argument("--sweep-first-seeds", default="",
+                    help="comma-separated first_seeds values (1 = Algorithm 1): the "
+                         "seeds-first variant's reads/s and accuracy, as --sweep-hmax")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up plus the timed steps only (no plain form, e2e or CPU "
                          "baseline): the command to run under ncu")
@@ -568,11 +571,11 @@ def accuracy(got, rd) -> dict:
             "not_found_pct": 100.0 * float((cls == 0).mean())}
 
 
-def run_sweep_hmax(args):
-    """h_max sweep (Ongoing Work, Observations: accuracy grows with h_max, throughput
-    falls): for each h_max, device-resident reads/s of the batched form over the
-    workload's reads, accuracy against the generator's truth, and a parity sample
-    against the oracle."""
+def run_sweep(args, param: str, values):
+    """Parameter sweep of the batched form: for each value of `param` (max_hits: the
+    h_max trade-off of Ongoing Work, Observations; first_seeds: the seeds-first variant
+    of Local Alignment), device-resident reads/s over the workload's reads, accuracy
+    against the generator's truth, and a parity sample against the oracle."""
     import torch
 
     import oracle
@@ -598,8 +601,8 @@ def run_sweep_hmax(args):
         sample.bases, sample.offsets, w.seed_len, w.num_seeds) if restricted else None)
     points = []
     with ClockSampler(0) as clk:
-        for h in [int(x) for x in args.sweep_hmax.split(",") if x.strip()]:
-            params = dict(w.params(), max_hits=h)
+        for h in values:
+            params = dict(w.params(), **{param: h})
 
             def step():
                 for b0 in range(0, n, batch):
@@ -626,10 +629,10 @@ def run_sweep_hmax(args):
                                 threads=os.cpu_count() or 1, **params)
             mism = sum(int((got[f][:sample.n] != ref[f]).sum())
                        for f in ("location", "edit_distance", "strand", "cls"))
-            points.append({"h_max": h, "reads_per_s": n * len(ms) / (sum(ms) / 1e3),
+            points.append({param: h, "reads_per_s": n * len(ms) / (sum(ms) / 1e3),
                            "ms_per_step": sum(ms) / len(ms), **accuracy(got, rd),
                            "parity_sample": {"reads": sample.n, "field_mismatches": mism}})
-    line = {"metric": METRIC, "mode": "sweep_hmax", "unit": "reads/s", "n_gpus": 1,
+    line = {"metric": METRIC, "mode": f"sweep_{param}", "unit": "reads/s", "n_gpus": 1,
             "dtype": "u8", "data": "synthetic",
             "config": {"workload": w.name, "genome_bp": w.G, "reads": n,
                        "correct_window_bases": CORRECT_WINDOW, "steps": args.steps,
@@ -646,7 +649,10 @@ def main():
     if args.serve:
         return run_serve(args)
     if args.sweep_hmax:
-        return run_sweep_hmax(args)
+        return run_sweep(args, "max_hits", [int(x) for x in args.sweep_hmax.split(",") if x])
+    if args.sweep_first_seeds:
+        return run_sweep(args, "first_seeds",
+                         [int(x) for x in args.sweep_first_seeds.split(",") if x])
     return run_ours(args)
 
 

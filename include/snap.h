@@ -63,6 +63,12 @@ typedef struct snap_server snap_server; /* opaque serving-loop state */
  *   max_dist_per_read  NULL, or one d_max per read overriding max_dist
  *              (a host pointer for snap_align / the server, a device pointer
  *              for the *_device calls).
+ *   first_seeds  0 or 1: Algorithm 1, one candidate scored after each seed.
+ *              k in [2, 2047]: the seeds-first variant the paper reports
+ *              trying (Local Alignment, the remark after the Baeza-Yates test):
+ *              the first k non-popular seeds (all of them when a read has fewer)
+ *              vote before the first candidate is scored, then one candidate
+ *              per seed as in Algorithm 1.
  */
 typedef struct {
     int32_t max_dist;
@@ -70,6 +76,7 @@ typedef struct {
     int32_t conf_diff;
     int32_t num_seeds;
     const int32_t* max_dist_per_read;
+    int32_t first_seeds;
 } snap_params;
 
 /*

@@ -74,7 +74,7 @@ def _load():
         lib.or_ed_pairs.restype = None
         lib.or_read_seed_kmers.argtypes = [vp, vp, u64, i32, i32, vp, u64]
         lib.or_read_seed_kmers.restype = u64
-        lib.or_align.argtypes = [vp, vp, vp, u64, i32, i32, i32, i32, vp, i32, i32, vp,
+        lib.or_align.argtypes = [vp, vp, vp, u64, i32, i32, i32, i32, i32, vp, i32, i32, vp,
                                  ctypes.POINTER(_Stats)]
         lib.or_align.restype = i32
         _lib = lib
@@ -193,8 +193,10 @@ class Index:
     def align(self, bases: np.ndarray, offsets: np.ndarray, max_dist: int = 8,
               max_hits: int = 300, conf_diff: int = 2, num_seeds: int = 0,
               max_dist_per_read: Optional[np.ndarray] = None, mode: int = 0,
-              threads: int = 1):
-        """Align reads; returns (results structured array, Stats)."""
+              threads: int = 1, first_seeds: int = 0):
+        """Align reads; returns (results structured array, Stats).  first_seeds > 1 runs
+        the seeds-first variant (that many non-popular seeds vote before the first
+        candidate is scored)."""
         bases = np.ascontiguousarray(bases, dtype=np.uint8)
         offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
         n = int(offsets.shape[0] - 1)
@@ -203,7 +205,8 @@ class Index:
                                                                           dtype=np.int32)
         st = _Stats()
         rc = _load().or_align(self._h, _p(bases), _p(offsets), n, max_dist, max_hits, conf_diff,
-                              num_seeds, _p(dpr), mode, threads, _p(out), ctypes.byref(st))
+                              num_seeds, first_seeds, _p(dpr), mode, threads, _p(out),
+                              ctypes.byref(st))
         if rc != 0:
             raise ValueError("oracle align: invalid input (non-ACGT base)")
         return out, Stats(**{f: int(getattr(st, f)) for f, _ in _Stats._fields_})

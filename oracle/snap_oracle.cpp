@@ -49,6 +49,12 @@
 //      (p, strand, d_best) when d_best <= d_max, else (-1, 0, -1);
 //      not found -> (-1, 0, -1).  "All seeds had > h_max entries" needs at
 //      least one seed; a read shorter than s is not found.
+//   R8 seeds-first variant (Local Alignment, the remark after the Baeza-Yates
+//      test that looking up more seeds before scoring the first candidate was
+//      tried): with first_seeds = k > 1, the first k non-popular seeds (all of
+//      them when there are fewer) add their votes before the first pick;
+//      from then on one pick per non-popular seed as in Algorithm 1.  No exit
+//      test can pass before the first score, so none is skipped.
 #include <algorithm>
 #include <climits>
 #include <cstdint>
@@ -175,6 +181,7 @@ int ed_dp(const uint8_t* x, int m, const uint8_t* t, int n) {
 
 struct Params {
     int d_max, h_max, c, n_seeds;
+    int first_seeds;  // <= 1: Algorithm 1; k > 1: the seeds-first variant (R8)
 };
 
 struct ReadResult {
@@ -349,6 +356,13 @@ ReadResult align_one(const OracleIndex& idx, const uint8_t* ascii, int m, const 
         }
     };
 
+    // R8: with first_seeds = k > 1 the first k non-popular seeds (all of them when
+    // there are fewer) vote before anything is scored; afterwards one candidate per
+    // seed as in Algorithm 1.  Before the first score no exit test can pass.
+    int last_nonpopular = -1;
+    for (int i = 0; i < n; ++i)
+        if (!popular[i]) last_nonpopular = i;
+    int voted = 0;
     bool returned = false;
     for (int i = 0; i < n && !returned; ++i) {
         if (popular[i]) continue;
@@ -356,6 +370,8 @@ ReadResult align_one(const OracleIndex& idx, const uint8_t* ascii, int m, const 
         for (int64_t p : fwd_p[i]) cand[2 * (uint64_t)p].votes++;
         for (int64_t p : rc_p[i]) cand[2 * (uint64_t)p + 1].votes++;
         if (pass0[i]) t++;
+        ++voted;
+        if (voted < P.first_seeds && i < last_nonpopular) continue;
         uint64_t k;
         if (pick(k)) score(k);
         if (d_best < c && d_second < d_best + c) {
@@ -585,10 +601,11 @@ uint64_t or_read_seed_kmers(const uint8_t* reads, const uint64_t* offsets, uint6
 
 // Align reads[offsets[r]..offsets[r+1]) for r < n.  mode 0 literal, 1
 // speculate-and-replay.  dmax_per_read overrides d_max per read when non-NULL.
+// first_seeds <= 1 is Algorithm 1, k > 1 its seeds-first variant (R8).
 // threads <= 0 means one.  Returns 0, or 1 on bad input (non-ACGT base).
 int or_align(void* h, const uint8_t* reads, const uint64_t* offsets, uint64_t n, int d_max,
-             int h_max, int c, int n_seeds, const int32_t* dmax_per_read, int mode, int threads,
-             or_result* out, or_stats* stats) {
+             int h_max, int c, int n_seeds, int first_seeds, const int32_t* dmax_per_read,
+             int mode, int threads, or_result* out, or_stats* stats) {
     const OracleIndex* idx = static_cast<OracleIndex*>(h);
     if (!idx || !reads || !offsets || !out) return 1;
     for (uint64_t r = 0; r < n; ++r)
@@ -600,7 +617,7 @@ int or_align(void* h, const uint8_t* reads, const uint64_t* offsets, uint64_t n,
     auto work = [&](int tix) {
         uint64_t r0 = n * tix / threads, r1 = n * (tix + 1) / threads;
         for (uint64_t r = r0; r < r1; ++r) {
-            Params P{dmax_per_read ? dmax_per_read[r] : d_max, h_max, c, n_seeds};
+            Params P{dmax_per_read ? dmax_per_read[r] : d_max, h_max, c, n_seeds, first_seeds};
             ReadResult rr = align_one(*idx, reads + offsets[r], (int)(offsets[r + 1] - offsets[r]),
                                       P, mode, st[tix]);
             out[r].location = rr.location;

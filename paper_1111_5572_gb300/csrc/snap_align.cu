@@ -275,6 +275,7 @@ struct FusedArgs {
     const unsigned long long* n_items_dev;  // when set, the item count is read from here
     unsigned long long* head;
     int d_max, h_max, c, num_seeds;
+    int first_seeds;  // non-popular seeds that vote before the first pick (<= 1: Algorithm 1)
     const int32_t* dmax_per_read;
     uint8_t shifts[32];
     int n_shifts;
@@ -674,6 +675,7 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
         __syncwarp();
         // ---- seeds and index probes, one lane per seed ----
         unsigned int H = 0;
+        int last_np = -1;  // last non-popular seed (for the seeds-first variant)
         for (int i = lane; i < n; i += 32) {
             bool p0 = false;
             const int o = seed_offset(i, m, s, a.shifts, a.n_shifts, &p0);
@@ -689,11 +691,15 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                 rec.flags |= kSeedPopular;
             } else {
                 H += (unsigned int)rec.fwd_n + rec.rc_n;
+                last_np = i;
             }
             wm.seeds[i] = rec;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) H += __shfl_xor_sync(kFull, H, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            H += __shfl_xor_sync(kFull, H, o);
+            last_np = max(last_np, __shfl_xor_sync(kFull, last_np, o));
+        }
         // ---- candidate table: shared memory when it fits, else this warp's global one ----
         uint32_t cap = 64;
         while (cap < 2u * H) cap <<= 1;
@@ -720,6 +726,7 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
             int nd = 0;        // distinct candidates so far (slots listed in dense)
             int qbuilt = 0;    // strands whose q-gram bitmap is built for this read
             int par_skip = 0;  // drain iterations before the parallel drain is retried
+            int voted = 0;     // non-popular seeds whose votes are in
             int d_best = kInf, d_second = kInf, nh = 0, t = 0;
             unsigned long long best_key = 0;
             bool any_nonpopular = false, returned = false;
@@ -897,6 +904,10 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                 }
                 __syncwarp();
                 if (rec.flags & kSeedPass0) ++t;
+                // seeds-first variant: the first first_seeds non-popular seeds (all
+                // of them when fewer remain) vote before the first pick; no exit
+                // test can pass before a score
+                if (++voted < a.first_seeds && i <= last_np) continue;
                 }
                 const unsigned long long pk = table_pick(tab, dense, nd, lane);
                 if (pk) {
@@ -1185,6 +1196,10 @@ int validate_params(const snap_index* idx, const snap_params* p) {
         set_error("max_hits %d outside [0, %u]", p->max_hits, kListMax);
         return SNAP_E_INVAL;
     }
+    if (p->first_seeds < 0 || p->first_seeds > kMaxSeeds) {
+        set_error("first_seeds %d outside [0, %d]", p->first_seeds, kMaxSeeds);
+        return SNAP_E_INVAL;
+    }
     if (p->num_seeds < 0 || p->num_seeds > kMaxSeeds) {
         set_error("num_seeds %d outside [0, %d]", p->num_seeds, kMaxSeeds);
         return SNAP_E_INVAL;
@@ -1354,6 +1369,7 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     a.h_max = p->max_hits;
     a.c = p->conf_diff;
     a.num_seeds = p->num_seeds;
+    a.first_seeds = p->first_seeds;
     a.dmax_per_read = p->max_dist_per_read;
     shift_list(idx->s, a.shifts, &a.n_shifts);
     a.out = d_out;
@@ -1934,6 +1950,7 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
     a.h_max = p->max_hits;
     a.c = p->conf_diff;
     a.num_seeds = p->num_seeds;
+    a.first_seeds = p->first_seeds;
     a.dmax_per_read = p->max_dist_per_read;
     shift_list(idx->s, a.shifts, &a.n_shifts);
     a.out = d_out;

@@ -53,6 +53,7 @@ struct LightArgs {
     uint64_t base0;
     uint64_t n;
     int d_max, h_max, c, num_seeds;
+    int first_seeds;
     const int32_t* dmax_per_read;
     uint8_t shifts[32];
     int n_shifts;
@@ -121,6 +122,7 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
             // seed lookups
             SeedRec seeds[kLightMaxSeeds];
             unsigned H = 0;
+            int last_np = -1;  // last non-popular seed (seeds-first variant)
             for (int i = 0; i < n; ++i) {
                 bool p0 = false;
                 const int o = seed_offset(i, m, s, a.shifts, a.n_shifts, &p0);
@@ -136,6 +138,7 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                     rec.flags |= kSeedPopular;
                 } else {
                     H += (unsigned)rec.fwd_n + rec.rc_n;
+                    last_np = i;
                 }
                 seeds[i] = rec;
             }
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                 int8_t cstate[kLightMaxCands];
                 unsigned long long hkey[kLightMaxCands];
                 int8_t hd[kLightMaxCands];
-                int nc = 0, nh = 0, t = 0;
+                int nc = 0, nh = 0, t = 0, voted = 0;
                 int d_best = kInfL, d_second = kInfL;
                 unsigned long long best_key = 0;
                 bool any_nonpopular = false, returned = false, draining = false;
@@ -186,6 +189,9 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                             ++cvotes[q];
                         }
                         if (rec.flags & kSeedPass0) ++t;
+                        // seeds-first variant: no pick before first_seeds non-popular
+                        // seeds (or all of them) have voted
+                        if (++voted < a.first_seeds && i <= last_np) continue;
                     }
                     // most-voted unscored candidate, ties to the smaller key
                     int pick = -1;
@@ -323,6 +329,7 @@ int launch_light(const snap_index* idx, Engine* e, const uint64_t* d_offsets, ui
     a.h_max = p->max_hits;
     a.c = p->conf_diff;
     a.num_seeds = p->num_seeds;
+    a.first_seeds = p->first_seeds;
     a.dmax_per_read = p->max_dist_per_read;
     shift_list(idx->s, a.shifts, &a.n_shifts);
     a.out = d_out;

@@ -44,6 +44,7 @@ struct PlainArgs {
     uint64_t n;
     int nmax;  // seed slots per read
     int d_max, h_max, c, num_seeds;
+    int first_seeds;  // seeds-first variant (<= 1: Algorithm 1)
     const int32_t* dmax_per_read;
     uint8_t shifts[32];
     int n_shifts;
@@ -348,6 +349,14 @@ __global__ void k_plain_replay(PlainArgs a) {
                     }
                 }
             };
+            // last non-popular seed, for the seeds-first variant
+            int last_np = -1;
+            for (int i = lane; i < nn; i += 32)
+                if (!(a.seeds[r * a.nmax + i].flags & kSeedPopular)) last_np = i;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                last_np = max(last_np, __shfl_xor_sync(kFull, last_np, o));
+            int voted = 0;
             uint64_t cur = base;
             for (int i = 0; i < nn; ++i) {
                 const SeedRec rec = a.seeds[r * a.nmax + i];
@@ -361,6 +370,7 @@ __global__ void k_plain_replay(PlainArgs a) {
                 cur += tot;
                 __syncwarp();
                 if (rec.flags & kSeedPass0) ++t;
+                if (++voted < a.first_seeds && i < last_np) continue;  // seeds-first
                 const unsigned long long pk = cap ? pick() : 0ull;
                 if (pk) score(pk);
                 if (d_best < c && d_second < d_best + c) {
@@ -423,6 +433,7 @@ int align_plain(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uin
     a.h_max = p->max_hits;
     a.c = p->conf_diff;
     a.num_seeds = p->num_seeds;
+    a.first_seeds = p->first_seeds;
     a.dmax_per_read = p->max_dist_per_read;
     shift_list(idx->s, a.shifts, &a.n_shifts);
     a.out = d_out;

@@ -182,6 +182,45 @@ def test_hand_built_branch_cases(snap):
             assert_same(got, ref, f"branch cases {kw}")
 
 
+def test_seeds_first_variant(snap):
+    # the hand-worked case of test_oracle_align.py (a 50 bp read: "multiple" under
+    # Algorithm 1, "single" when both seeds vote first) in all three kernels of the
+    # batched form (thread per read, warp per read after a give-up, team mode is for
+    # long reads and tested below) and the plain form; then whole workloads
+    g = bytearray(np.frombuffer(b"ACGT", dtype=np.uint8)[
+        np.random.default_rng(17).integers(0, 4, 20_000)].tobytes())
+    read = bytes(np.frombuffer(b"ACGT", dtype=np.uint8)[
+        np.random.default_rng(18).integers(0, 4, 50)].tobytes())
+
+    def sub(a, i):
+        a = bytearray(a)
+        a[i] = b"CGTA"[b"ACGT".index(a[i])]
+        return bytes(a)
+
+    g[9000:9050] = sub(read, 45)
+    g[2000:2050] = sub(sub(read, 25), 35)
+    gn = np.frombuffer(bytes(g), dtype=np.uint8)
+    gi = snap.Index(gn, 20)
+    bases = np.frombuffer(read, dtype=np.uint8)
+    offs = np.array([0, 50], dtype=np.uint64)
+    for k, cls in ((0, 2), (1, 2), (2, 1), (5, 1)):
+        for plain in (False, True):
+            got = gi.align(bases, offs, plain=plain, first_seeds=k)
+            assert (int(got["location"][0]), int(got["cls"][0])) == (9000, cls), (k, plain)
+    with pytest.raises(snap.SnapError):
+        gi.align(bases, offs, first_seeds=-1)
+    for name, G, n, dpr_rule in (("C2", 3_000_000, 20_000, False), ("C5", 10_000_000, 30_000, False),
+                                 ("C4", 2_000_000, 300, True)):
+        w = synth.CONFIGS[name].scaled(G=G, n_reads=n)
+        g2, _ = w.make_genome()
+        rd = w.make_reads(g2, n=n)
+        dpr = w.max_dist_per_read(rd.lengths()) if dpr_rule else None
+        for k in (3, 5):
+            for plain in (False, True):
+                got, ref, _ = _run_both(snap, g2, rd, w, plain=plain, dpr=dpr, first_seeds=k)
+                assert_same(got, ref, f"{name} first_seeds={k} plain={plain}")
+
+
 def test_autotune_and_graph_replay_keep_results(snap):
     # launch shapes and graph replay must never change a result: compare against the
     # untuned, ungraphed run on several batch sizes, through the graph update path

@@ -247,3 +247,66 @@ def test_replay_mode_and_filtered_index_agree(cfg, G, n):
     r2, _ = filt.align(rd.bases, rd.offsets, max_dist_per_read=dpr, threads=4, **w.params())
     assert np.array_equal(r0, r2)
     assert st.n_single > 0.6 * n  # long indels (up to 20 bases) push some reads past d_max
+
+
+def _align_first(genome: bytes, reads, first_seeds, **kw):
+    idx = oracle.Index(np.frombuffer(bytes(genome), dtype=np.uint8), S)
+    bases = np.frombuffer(b"".join(reads), dtype=np.uint8)
+    offs = np.zeros(len(reads) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum([len(r) for r in reads])
+    params = dict(max_dist=8, max_hits=300, conf_diff=2, num_seeds=0, first_seeds=first_seeds)
+    params.update(kw)
+    res, st = idx.align(bases, offs, **params)
+    res1, _ = idx.align(bases, offs, mode=1, **params)
+    assert np.array_equal(res, res1), "replay mode disagrees with literal mode"
+    return res, st
+
+
+def test_seeds_first_variant_changes_the_outcome():
+    # A 50 bp read has two seeds, at 0 and 20.  B (9000) is the read with one
+    # substitution at base 45 (outside both seeds): d = 1, voted by both seeds.
+    # A (2000) is the read with substitutions at 25 and 35: d = 2, voted by seed 0
+    # only.
+    # Algorithm 1 (first_seeds 0 or 1): after seed 0, A and B have one vote each and
+    # the smaller key A is scored at L = d_max+c-1: d_best = 2.  After seed 1, B (two
+    # votes) is scored at L = d_best+c-1 = 3: d = 1, so d_best = 1 and d_second = 2
+    # (A, another bucket): d_best < c and d_second < d_best+c, return "multiple" at
+    # B after two distance calls.
+    # Seeds-first with k = 2 (or any k >= 2, the read having only two non-popular
+    # seeds): both seeds vote first, B leads 2 to 1 and is scored: d_best = 1, no
+    # second; no exit passes (t = 2 < d_best+c = 3) and the seeds run out, so the
+    # read is a single hit at B after one call; A is never scored.
+    g = _rand(20_000, 17)
+    read = bytes(_rand(50, 18))
+    g[9000:9050] = _sub(read, 45)
+    g[2000:2050] = _sub(_sub(read, 25), 35)
+    g = bytes(g)
+    assert oracle.ed_dp(read, g[9000:9100]) == 1 and oracle.ed_dp(read, g[2000:2100]) == 2
+    for k in (0, 1):
+        res, st = _align_first(g, [read], k)
+        assert _tup(res[0]) == (9000, 0, 1, MULTI) and st.ed_calls == 2
+    for k in (2, 5):
+        res, st = _align_first(g, [read], k)
+        assert _tup(res[0]) == (9000, 0, 1, SINGLE) and st.ed_calls == 1
+
+
+def test_seeds_first_one_equals_algorithm_1_on_workloads():
+    # first_seeds 0 and 1 are both Algorithm 1; larger values differ only in order
+    # and never find a distance that is not the table's at the reported location
+    w = synth.CONFIGS["C2"].scaled(G=1_000_000, n_reads=3000)
+    g, _ = w.make_genome()
+    rd = w.make_reads(g)
+    idx = oracle.Index(g, w.seed_len)
+    base, _ = idx.align(rd.bases, rd.offsets, **w.params())
+    one, _ = idx.align(rd.bases, rd.offsets, first_seeds=1, **w.params())
+    assert np.array_equal(base, one)
+    three, st3 = idx.align(rd.bases, rd.offsets, first_seeds=3, **w.params())
+    replay, _ = idx.align(rd.bases, rd.offsets, first_seeds=3, mode=1, **w.params())
+    assert np.array_equal(three, replay)
+    hit = np.nonzero(three["location"] >= 0)[0][:200]
+    for i in hit:
+        x = bytes(rd.bases[rd.offsets[i]:rd.offsets[i + 1]])
+        if three["strand"][i]:
+            x = _rc(x)
+        p = int(three["location"][i])
+        assert oracle.ed_dp(x, bytes(g[p:p + len(x) + 20])) == three["edit_distance"][i]
