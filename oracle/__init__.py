@@ -56,7 +56,7 @@ def _load():
         build()
         lib = ctypes.CDLL(_LIB)
         vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
-        lib.or_index_build.argtypes = [vp, u64, i32, vp, u64, ctypes.POINTER(ctypes.c_int)]
+        lib.or_index_build.argtypes = [vp, u64, i32, i32, vp, u64, ctypes.POINTER(ctypes.c_int)]
         lib.or_index_build.restype = vp
         lib.or_index_free.argtypes = [vp]
         lib.or_index_free.restype = None
@@ -164,19 +164,20 @@ class Index:
     """Sorted-array index of every overlapping s-mer (optionally restricted to a key set)."""
 
     def __init__(self, genome_ascii: np.ndarray, seed_len: int,
-                 kmer_filter: Optional[np.ndarray] = None):
+                 kmer_filter: Optional[np.ndarray] = None, stride: int = 1):
         lib = _load()
         self._genome = np.ascontiguousarray(genome_ascii, dtype=np.uint8)
         err = ctypes.c_int(0)
         filt = None if kmer_filter is None else np.ascontiguousarray(kmer_filter, dtype=np.uint64)
         t0 = time.perf_counter()
-        h = lib.or_index_build(_p(self._genome), self._genome.shape[0], seed_len, _p(filt),
-                               0 if filt is None else filt.shape[0], ctypes.byref(err))
+        h = lib.or_index_build(_p(self._genome), self._genome.shape[0], seed_len, int(stride),
+                               _p(filt), 0 if filt is None else filt.shape[0], ctypes.byref(err))
         self.build_seconds = time.perf_counter() - t0
         if not h:
             raise ValueError(f"oracle index build failed (code {err.value})")
         self._h = h
         self.seed_len = seed_len
+        self.stride = int(stride)
         self.G = int(self._genome.shape[0])
 
     @property

@@ -55,6 +55,16 @@
 //      them when there are fewer) add their votes before the first pick;
 //      from then on one pick per non-popular seed as in Algorithm 1.  No exit
 //      test can pass before the first score, so none is skipped.
+//   R9 stride-k index (Hash Index, Overlapping Seeds footnote: a window slid k
+//      bases at a time gives a k-times smaller index and more lookups): only
+//      positions l with l % k == 0 are indexed, and each seed of the R2 order
+//      at offset o is looked up at o, o+1, ..., o+k-1 (those that fit), so an
+//      error-free seed meets exactly one indexed position whatever the
+//      alignment.  A probe is popular on its own count (indexed occurrences);
+//      a seed votes with its non-popular probes and is skipped when all are
+//      popular; it counts toward t (pass 0 seeds tested) only when none of its
+//      probes was popular, since a skipped probe may be the one that meets the
+//      index.  With k = 1 a probe is a seed and this is Algorithm 1.
 #include <algorithm>
 #include <climits>
 #include <cstdint>
@@ -87,6 +97,7 @@ uint64_t kmer_value(const uint8_t* codes, int s) {
 
 struct OracleIndex {
     int s = 0;
+    int stride = 1;  // R9: only positions l with l % stride == 0 are indexed
     uint64_t G = 0;
     std::vector<uint8_t> genome;                            // codes 0..3
     std::vector<std::pair<uint64_t, uint32_t>> entries;     // (s-mer, position), sorted
@@ -251,11 +262,22 @@ ReadResult align_one(const OracleIndex& idx, const uint8_t* ascii, int m, const 
     bool any_nonpopular = false;
     const int d_max = P.d_max, c = P.c;
 
-    // seed lookups: the two position lists of each seed
-    std::vector<std::vector<int64_t>> fwd_p(n), rc_p(n);
-    std::vector<uint8_t> popular(n, 0);
-    for (int i = 0; i < n; ++i) {
-        const int o = offs[i];
+    // R9: seed g of the order above is looked up at offsets o, o+1, ..., o+stride-1
+    // (those that fit in the read), so that one of them meets an indexed position
+    // whatever the alignment; with stride 1 a probe is a seed.
+    const int stride = idx.stride;
+    std::vector<int> probe_off, probe_group;
+    for (int g = 0; g < n; ++g)
+        for (int j = 0; j < stride && offs[g] + j + s <= m; ++j) {
+            probe_off.push_back(offs[g] + j);
+            probe_group.push_back(g);
+        }
+    const int np = (int)probe_off.size();
+    // probe lookups: the two position lists of each probe
+    std::vector<std::vector<int64_t>> fwd_p(np), rc_p(np);
+    std::vector<uint8_t> popular(np, 0);
+    for (int i = 0; i < np; ++i) {
+        const int o = probe_off[i];
         std::vector<uint8_t> S(R.begin() + o, R.begin() + o + s);
         std::vector<uint8_t> Src(s);
         for (int j = 0; j < s; ++j) Src[j] = (uint8_t)(3 - S[s - 1 - j]);
@@ -291,7 +313,7 @@ ReadResult align_one(const OracleIndex& idx, const uint8_t* ascii, int m, const 
     std::map<uint64_t, int> d0;
     const int L0 = d_max + c - 1;
     if (mode == 1) {
-        for (int i = 0; i < n; ++i) {
+        for (int i = 0; i < np; ++i) {
             for (int64_t p : fwd_p[i]) d0.emplace(2 * (uint64_t)p, 0);
             for (int64_t p : rc_p[i]) d0.emplace(2 * (uint64_t)p + 1, 0);
         }
@@ -359,19 +381,33 @@ ReadResult align_one(const OracleIndex& idx, const uint8_t* ascii, int m, const 
     // R8: with first_seeds = k > 1 the first k non-popular seeds (all of them when
     // there are fewer) vote before anything is scored; afterwards one candidate per
     // seed as in Algorithm 1.  Before the first score no exit test can pass.
+    // A seed counts as non-popular when one of its probes is (its votes are those
+    // of its non-popular probes) and as tested for the Baeza-Yates bound (t) only
+    // when it is from the unshifted pass and none of its probes was popular.
+    std::vector<uint8_t> any_np(n, 0), all_np(n, 1);
+    for (int i = 0; i < np; ++i) {
+        if (popular[i]) all_np[probe_group[i]] = 0;
+        else any_np[probe_group[i]] = 1;
+    }
     int last_nonpopular = -1;
-    for (int i = 0; i < n; ++i)
-        if (!popular[i]) last_nonpopular = i;
+    for (int g = 0; g < n; ++g)
+        if (any_np[g]) last_nonpopular = g;
     int voted = 0;
     bool returned = false;
-    for (int i = 0; i < n && !returned; ++i) {
-        if (popular[i]) continue;
+    int pi = 0;  // first probe of seed g
+    for (int g = 0; g < n && !returned; ++g) {
+        const int p0 = pi;
+        while (pi < np && probe_group[pi] == g) ++pi;
+        if (!any_np[g]) continue;
         any_nonpopular = true;
-        for (int64_t p : fwd_p[i]) cand[2 * (uint64_t)p].votes++;
-        for (int64_t p : rc_p[i]) cand[2 * (uint64_t)p + 1].votes++;
-        if (pass0[i]) t++;
+        for (int i = p0; i < pi; ++i) {
+            if (popular[i]) continue;
+            for (int64_t p : fwd_p[i]) cand[2 * (uint64_t)p].votes++;
+            for (int64_t p : rc_p[i]) cand[2 * (uint64_t)p + 1].votes++;
+        }
+        if (pass0[g] && all_np[g]) t++;
         ++voted;
-        if (voted < P.first_seeds && i < last_nonpopular) continue;
+        if (voted < P.first_seeds && g < last_nonpopular) continue;
         uint64_t k;
         if (pick(k)) score(k);
         if (d_best < c && d_second < d_best + c) {
@@ -390,7 +426,7 @@ ReadResult align_one(const OracleIndex& idx, const uint8_t* ascii, int m, const 
         if (best == 0) st.first_scored_is_best++;
     }
     if (!returned) {
-        bool all_popular = (n >= 1) && !any_nonpopular;
+        bool all_popular = (np >= 1) && !any_nonpopular;
         if (d_best <= d_max && d_second >= d_best + c) {
             res.cls = kSingle;
             res.location = (int64_t)(hits[best].key >> 1);
@@ -427,15 +463,16 @@ struct or_stats {
 // Build the oracle index over genome_ascii[0..G).  When filter != NULL (nfilter
 // sorted s-mer values, first base most significant), only entries whose s-mer
 // is in the filter are kept.  Returns NULL and sets *err on bad input.
-void* or_index_build(const uint8_t* genome_ascii, uint64_t G, int s, const uint64_t* filter,
-                     uint64_t nfilter, int* err) {
+void* or_index_build(const uint8_t* genome_ascii, uint64_t G, int s, int stride,
+                     const uint64_t* filter, uint64_t nfilter, int* err) {
     if (err) *err = 0;
-    if (!genome_ascii || s < 1 || s > 32 || G < (uint64_t)s) {
+    if (!genome_ascii || s < 1 || s > 32 || G < (uint64_t)s || stride < 1) {
         if (err) *err = 1;
         return nullptr;
     }
     OracleIndex* idx = new OracleIndex();
     idx->s = s;
+    idx->stride = stride;
     idx->G = G;
     idx->genome.resize(G);
     for (uint64_t i = 0; i < G; ++i) {
@@ -461,7 +498,7 @@ void* or_index_build(const uint8_t* genome_ascii, uint64_t G, int s, const uint6
         uint64_t v = kmer_value(idx->genome.data(), s);
         for (uint64_t l = 0; l < npos; ++l) {
             if (l > 0) v = ((v << 2) | idx->genome[l + s - 1]) & mask;
-            idx->entries.emplace_back(v, (uint32_t)l);
+            if (l % (uint64_t)stride == 0) idx->entries.emplace_back(v, (uint32_t)l);
         }
     } else {
         // Restricted build: a bitmap of hashed filter keys screens each window
@@ -482,6 +519,7 @@ void* or_index_build(const uint8_t* genome_ascii, uint64_t G, int s, const uint6
             uint64_t v = kmer_value(idx->genome.data() + l0, s);
             for (uint64_t l = l0; l < l1; ++l) {
                 if (l > l0) v = ((v << 2) | idx->genome[l + s - 1]) & mask;
+                if (l % (uint64_t)stride != 0) continue;
                 const uint64_t hv = h(v);
                 if (!(bits[hv >> 6] >> (hv & 63) & 1)) continue;
                 if (std::binary_search(filt.begin(), filt.end(), v))

@@ -310,3 +310,49 @@ def test_seeds_first_one_equals_algorithm_1_on_workloads():
             x = _rc(x)
         p = int(three["location"][i])
         assert oracle.ed_dp(x, bytes(g[p:p + len(x) + 20])) == three["edit_distance"][i]
+
+
+@pytest.mark.parametrize("stride", [2, 3, 5])
+def test_strided_index_error_free_reads_at_every_phase(stride):
+    # With a stride-k index each seed is looked up at k consecutive offsets, so an
+    # error-free read from unique sequence meets the index whatever its origin modulo
+    # k: single hit at the origin with distance 0, on both strands.
+    g = bytes(_rand(30_000, 21))
+    idx = oracle.Index(np.frombuffer(g, dtype=np.uint8), S, stride=stride)
+    reads, expect = [], []
+    for q in range(stride):
+        p = 1000 + 997 * q + q  # every residue of p modulo the stride
+        reads += [g[p:p + 100], _rc(g[p + 5000:p + 5100])]
+        expect += [(p, 0, 0, SINGLE), (p + 5000, 1, 0, SINGLE)]
+    bases = np.frombuffer(b"".join(reads), dtype=np.uint8)
+    offs = np.zeros(len(reads) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum([len(r) for r in reads])
+    res, st = idx.align(bases, offs, max_dist=8, max_hits=300, conf_diff=2)
+    assert [_tup(r) for r in res] == expect
+    # seeds at 0, 20, 40, 60 get k probes; the one at 80 has room for one (80 + 20 = m)
+    assert st.seeds_looked_up == len(reads) * (4 * stride + 1)
+    res1, _ = idx.align(bases, offs, max_dist=8, max_hits=300, conf_diff=2, mode=1)
+    assert np.array_equal(res, res1)
+
+
+def test_strided_index_workloads_stride_one_and_replay():
+    # stride 1 is the plain index; for larger strides the replay mode equals the
+    # literal one and every reported distance is the table's at the reported place
+    w = synth.CONFIGS["C2"].scaled(G=1_000_000, n_reads=2000)
+    g, _ = w.make_genome()
+    rd = w.make_reads(g)
+    base, _ = oracle.Index(g, w.seed_len).align(rd.bases, rd.offsets, **w.params())
+    one, _ = oracle.Index(g, w.seed_len, stride=1).align(rd.bases, rd.offsets, **w.params())
+    assert np.array_equal(base, one)
+    for stride in (2, 4):
+        idx = oracle.Index(g, w.seed_len, stride=stride)
+        lit, st = idx.align(rd.bases, rd.offsets, **w.params())
+        rep, _ = idx.align(rd.bases, rd.offsets, mode=1, **w.params())
+        assert np.array_equal(lit, rep)
+        assert (lit["cls"] == SINGLE).mean() > 0.85
+        for i in np.nonzero(lit["location"] >= 0)[0][:150]:
+            x = bytes(rd.bases[rd.offsets[i]:rd.offsets[i + 1]])
+            if lit["strand"][i]:
+                x = _rc(x)
+            p = int(lit["location"][i])
+            assert oracle.ed_dp(x, bytes(g[p:p + len(x) + 20])) == lit["edit_distance"][i]

@@ -117,3 +117,24 @@ def test_index_rejects_bad_input():
         oracle.Index(np.frombuffer(b"ACGTNACGTACGTACGTACGT", dtype=np.uint8), 8)
     with pytest.raises(ValueError):
         oracle.Index(np.frombuffer(b"ACGT", dtype=np.uint8), 8)
+
+
+@pytest.mark.parametrize("stride", [2, 3, 4])
+def test_strided_index_matches_brute_force_scan(stride):
+    # stride-k index (Overlapping Seeds footnote): exactly the windows starting at a
+    # multiple of k, every other window absent
+    s = 12
+    g = bytearray(_rand_genome(20_000, 6).tobytes())
+    unit = bytes(g[100:140])
+    for pos in (3001, 7002, 15003):
+        g[pos:pos + 40] = unit
+    g = bytes(g)
+    idx = oracle.Index(np.frombuffer(g, dtype=np.uint8), s, stride=stride)
+    assert idx.entries == (len(g) - s) // stride + 1
+    rng = np.random.default_rng(10)
+    queries = [g[100:100 + s], g[101:101 + s], g[len(g) - s:], g[0:s]]
+    for _ in range(300):
+        l = int(rng.integers(0, len(g) - s + 1))
+        queries.append(g[l:l + s])
+    for q in queries:
+        assert idx.occurrences(q) == [p for p in _brute_positions(g, q) if p % stride == 0], q
