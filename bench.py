@@ -69,6 +69,9 @@ def _args():
     ap.add_argument("--sweep-first-seeds", default="",
                     help="comma-separated first_seeds values (1 = Algorithm 1): the "
                          "seeds-first variant's reads/s and accuracy, as --sweep-hmax")
+    ap.add_argument("--stride", type=int, default=1,
+                    help="stride-k index: index windows at multiples of k, probe each seed "
+                         "at k offsets (1 = every window, the default)")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up plus the timed steps only (no plain form, e2e or CPU "
                          "baseline): the command to run under ncu")
@@ -193,7 +196,8 @@ def make_workload(args, rank: int):
     return w, g, rd, dpr, time.perf_counter() - t0
 
 
-def cpu_oracle_sample(w, g, rd, dpr, target_s: float = 12.0, max_reads: int = 400_000):
+def cpu_oracle_sample(w, g, rd, dpr, target_s: float = 12.0, max_reads: int = 400_000,
+                      stride: int = 1):
     """Time the oracle (as it stands) on a bounded sample on all host cores."""
     import oracle
     cores = os.cpu_count() or 1
@@ -204,9 +208,9 @@ def cpu_oracle_sample(w, g, rd, dpr, target_s: float = 12.0, max_reads: int = 40
         max_reads = min(max_reads, 100_000)
         cand = rd.subset(np.arange(min(rd.n, max_reads)))
         idx = oracle.Index(g, w.seed_len, kmer_filter=oracle.read_seed_kmers(
-            cand.bases, cand.offsets, w.seed_len, w.num_seeds))
+            cand.bases, cand.offsets, w.seed_len, w.num_seeds, stride), stride=stride)
     else:
-        idx = oracle.Index(g, w.seed_len)
+        idx = oracle.Index(g, w.seed_len, stride=stride)
     probe = rd.subset(np.arange(min(rd.n, 20_000)))
     pd = None if dpr is None else dpr[:probe.n]
     t0 = time.perf_counter()
@@ -234,7 +238,7 @@ def run_reference(args):
     import oracle
     w, g, rd, dpr, _ = make_workload(args, 0)
     cores = os.cpu_count() or 1
-    idx = oracle.Index(g, w.seed_len)
+    idx = oracle.Index(g, w.seed_len, stride=args.stride)
     per_step = min(rd.n, 10_000)
 
     def step(k):
@@ -284,7 +288,7 @@ def run_ours(args):
     w, g, rd, dpr, gen_s = make_workload(args, rank)
     n = rd.n
     t0 = time.perf_counter()
-    idx = snap.Index(g, w.seed_len)
+    idx = snap.Index(g, w.seed_len, stride=args.stride)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     info = idx.info()
@@ -397,7 +401,8 @@ def run_ours(args):
         "config": {"workload": w.name, "genome_bp": w.G, "repeat_frac": w.repeat_frac,
                    "reads_per_step": n, "reads_per_call": batch,
                    "read_len": "100" if w.len_mode == 0 else "mixed",
-                   "seed_len": w.seed_len, **params, "form": args.form,
+                   "seed_len": w.seed_len, "index_stride": args.stride, **params,
+                   "form": args.form,
                    "l2": "flushed between steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "bases_per_s": value * float(rd.lengths().mean()),
@@ -467,7 +472,7 @@ def run_ours(args):
                        "d2h_bytes_per_step": int(16 * n), "steps": args.e2e_steps}
 
     if rank == 0 and not args.no_cpu_baseline:
-        cb, sample, ref = cpu_oracle_sample(w, g, rd, dpr)
+        cb, sample, ref = cpu_oracle_sample(w, g, rd, dpr, stride=args.stride)
         line["cpu_baseline"] = cb
         mism = sum(int((got[f][sample] != ref[f]).sum()) for f in
                    ("location", "edit_distance", "strand", "cls"))
@@ -587,7 +592,7 @@ def run_sweep(args, param: str, values):
     dev = torch.device("cuda", 0)
     w, g, rd, dpr, gen_s = make_workload(args, 0)
     n = rd.n
-    idx = snap.Index(g, w.seed_len)
+    idx = snap.Index(g, w.seed_len, stride=args.stride)
     d_b = torch.from_numpy(rd.bases).to(dev)
     d_o = torch.from_numpy(rd.offsets.view(np.int64)).to(dev)
     d_out = torch.zeros((n, 16), dtype=torch.uint8, device=dev)
@@ -598,7 +603,8 @@ def run_sweep(args, param: str, values):
     sample = rd.subset(np.arange(min(n, 20_000)))
     restricted = w.G > 500_000_000
     oidx = oracle.Index(g, w.seed_len, kmer_filter=oracle.read_seed_kmers(
-        sample.bases, sample.offsets, w.seed_len, w.num_seeds) if restricted else None)
+        sample.bases, sample.offsets, w.seed_len, w.num_seeds, args.stride)
+        if restricted else None, stride=args.stride)
     points = []
     with ClockSampler(0) as clk:
         for h in values:
@@ -634,7 +640,7 @@ def run_sweep(args, param: str, values):
                            "parity_sample": {"reads": sample.n, "field_mismatches": mism}})
     line = {"metric": METRIC, "mode": f"sweep_{param}", "unit": "reads/s", "n_gpus": 1,
             "dtype": "u8", "data": "synthetic",
-            "config": {"workload": w.name, "genome_bp": w.G, "reads": n,
+            "config": {"workload": w.name, "genome_bp": w.G, "reads": n, "index_stride": args.stride,
                        "correct_window_bases": CORRECT_WINDOW, "steps": args.steps,
                        "l2": "flushed between steps (512 MiB write)"},
             "points": points, "clocks": clk.summary()}

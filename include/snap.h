@@ -97,7 +97,7 @@ typedef struct {
 typedef struct {
     uint64_t genome_len;
     int32_t seed_len;
-    int32_t reserved;
+    int32_t stride;         /* indexed windows start at multiples of this (1: every one) */
     uint64_t table_slots;     /* open-addressing slots (16 bytes each, 4 per bucket) */
     uint64_t distinct_seeds;  /* occupied slots: distinct canonical s-mers */
     uint64_t list_entries;    /* positions stored out of line (keys seen 2..65534 times) */
@@ -118,6 +118,22 @@ typedef struct {
  */
 int snap_index_build(const uint8_t* genome_ascii, uint64_t genome_len, int seed_len,
                      snap_index** out);
+
+/*
+ * The same with a stride-k index (Hash Index, the Overlapping Seeds footnote:
+ * sliding the window k bases at a time gives a k-times smaller index at the cost
+ * of more lookups): only windows starting at multiples of `stride` are indexed,
+ * and every align call on this index looks each seed up at its offset and the
+ * stride - 1 offsets after it (those that fit in the read), so that an
+ * error-free seed meets one indexed window whatever the alignment.  A seed votes
+ * with its non-popular probes, is skipped when all are popular, and counts
+ * toward Algorithm 1's "non-overlapping seeds tested" only when none of its
+ * probes was popular.  stride 1 is snap_index_build.
+ *   stride   k in [1, 16]; a read may use at most 2047 seeds whatever k is.
+ * Errors: as snap_index_build, and SNAP_E_INVAL for a stride outside [1, 16].
+ */
+int snap_index_build_stride(const uint8_t* genome_ascii, uint64_t genome_len, int seed_len,
+                            int stride, snap_index** out);
 
 /* Free an index and its device memory.  NULL is accepted. */
 int snap_index_free(snap_index* index);

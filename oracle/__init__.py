@@ -72,7 +72,7 @@ def _load():
         lib.or_ed_dp.restype = i32
         lib.or_ed_pairs.argtypes = [vp, vp, vp, vp, vp, u64, vp, vp]
         lib.or_ed_pairs.restype = None
-        lib.or_read_seed_kmers.argtypes = [vp, vp, u64, i32, i32, vp, u64]
+        lib.or_read_seed_kmers.argtypes = [vp, vp, u64, i32, i32, i32, vp, u64]
         lib.or_read_seed_kmers.restype = u64
         lib.or_align.argtypes = [vp, vp, vp, u64, i32, i32, i32, i32, i32, vp, i32, i32, vp,
                                  ctypes.POINTER(_Stats)]
@@ -134,12 +134,13 @@ def seed_offsets(m: int, s: int, n: int):
     return offs[:k].tolist(), p0[:k].astype(bool).tolist()
 
 
-def read_seed_kmers(bases: np.ndarray, offsets: np.ndarray, s: int, n_seeds: int) -> np.ndarray:
+def read_seed_kmers(bases: np.ndarray, offsets: np.ndarray, s: int, n_seeds: int,
+                    stride: int = 1) -> np.ndarray:
     lib = _load()
     n = int(offsets.shape[0] - 1)
-    need = lib.or_read_seed_kmers(_p(bases), _p(offsets), n, s, n_seeds, None, 0)
+    need = lib.or_read_seed_kmers(_p(bases), _p(offsets), n, s, n_seeds, stride, None, 0)
     out = np.zeros(max(1, need), dtype=np.uint64)
-    lib.or_read_seed_kmers(_p(bases), _p(offsets), n, s, n_seeds, _p(out), need)
+    lib.or_read_seed_kmers(_p(bases), _p(offsets), n, s, n_seeds, stride, _p(out), need)
     return np.unique(out[:need])
 
 

@@ -606,20 +606,25 @@ void or_ed_pairs(const uint8_t* xs, const uint64_t* xoff, const uint8_t* ts, con
     }
 }
 
-// The s-mer values of every seed of every read and of their reverse
-// complements (the lookups Algorithm 1 makes), for a filtered index.  Returns
+// The s-mer values of every seed of every read (every probe of it, R9, for a
+// strided index) and of their reverse complements (the lookups Algorithm 1
+// makes), for a filtered index.  Returns
 // the number written (<= cap) or the number needed when out == NULL.
 uint64_t or_read_seed_kmers(const uint8_t* reads, const uint64_t* offsets, uint64_t nreads, int s,
-                            int n_seeds, uint64_t* out, uint64_t cap) {
+                            int n_seeds, int stride, uint64_t* out, uint64_t cap) {
     uint64_t k = 0;
-    std::vector<int> offs;
+    std::vector<int> offs, probes;
     std::vector<uint8_t> pass0, S(s), Src(s);
+    if (stride < 1) stride = 1;
     for (uint64_t r = 0; r < nreads; ++r) {
         const uint8_t* a = reads + offsets[r];
         int m = (int)(offsets[r + 1] - offsets[r]);
         int n = n_seeds > 0 ? n_seeds : (s > 0 ? m / s : 0);
         seed_offsets(m, s, n, offs, pass0);
-        for (int o : offs) {
+        probes.clear();  // R9: each seed's probes
+        for (int o0 : offs)
+            for (int j = 0; j < stride && o0 + j + s <= m; ++j) probes.push_back(o0 + j);
+        for (int o : probes) {
             bool ok = true;
             for (int j = 0; j < s; ++j) {
                 int c = code_of(a[o + j]);

@@ -24,7 +24,7 @@ RESULT_DTYPE = np.dtype([("location", "<i8"), ("edit_distance", "<i4"), ("strand
 assert RESULT_DTYPE.itemsize == 16
 
 # every symbol include/snap.h declares
-EXPORTS = ("snap_index_build", "snap_index_free", "snap_index_info_get", "snap_align",
+EXPORTS = ("snap_index_build", "snap_index_build_stride", "snap_index_free", "snap_index_info_get", "snap_align",
            "snap_align_device", "snap_align_plain_device", "snap_align_plain",
            "snap_server_create", "snap_server_submit", "snap_server_wait", "snap_server_destroy",
            "snap_last_call_stats", "snap_align_device_noalloc", "snap_index_configure",
@@ -46,7 +46,7 @@ class snap_params(ctypes.Structure):
 
 class snap_index_info(ctypes.Structure):
     _fields_ = [("genome_len", ctypes.c_uint64), ("seed_len", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("table_slots", ctypes.c_uint64),
+                ("stride", ctypes.c_int32), ("table_slots", ctypes.c_uint64),
                 ("distinct_seeds", ctypes.c_uint64), ("list_entries", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64), ("build_seconds", ctypes.c_double)]
 
@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH):
     vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
     P = ctypes.POINTER
     lib.snap_index_build.argtypes = [vp, u64, i32, P(vp)]
+    lib.snap_index_build_stride.argtypes = [vp, u64, i32, i32, P(vp)]
     lib.snap_index_free.argtypes = [vp]
     lib.snap_index_info_get.argtypes = [vp, P(snap_index_info)]
     for name in ("snap_align", "snap_align_plain"):
@@ -132,14 +133,19 @@ def measure_gather(buffer_bytes: int = 8 << 30, chunk_bytes: int = 32,
 class Index:
     """Device-resident seed index of one genome (snap_index_build)."""
 
-    def __init__(self, genome_ascii: np.ndarray, seed_len: int = 20):
+    def __init__(self, genome_ascii: np.ndarray, seed_len: int = 20, stride: int = 1):
         lib = load_library()
         g = np.ascontiguousarray(genome_ascii, dtype=np.uint8)
         h = ctypes.c_void_p()
-        _check(lib.snap_index_build(_p(g), g.shape[0], int(seed_len), ctypes.byref(h)),
-               "snap_index_build")
+        if stride == 1:
+            _check(lib.snap_index_build(_p(g), g.shape[0], int(seed_len), ctypes.byref(h)),
+                   "snap_index_build")
+        else:
+            _check(lib.snap_index_build_stride(_p(g), g.shape[0], int(seed_len), int(stride),
+                                               ctypes.byref(h)), "snap_index_build_stride")
         self._h = h
         self.seed_len = seed_len
+        self.stride = int(stride)
         self.G = int(g.shape[0])
 
     @property
@@ -149,7 +155,7 @@ class Index:
     def info(self) -> dict:
         inf = snap_index_info()
         _check(load_library().snap_index_info_get(self._h, ctypes.byref(inf)), "info")
-        return {f: getattr(inf, f) for f, _ in snap_index_info._fields_ if f != "reserved"}
+        return {f: getattr(inf, f) for f, _ in snap_index_info._fields_}
 
     def configure(self, autotune: bool = True, cuda_graphs: bool = True, team: int = -1):
         """snap_index_configure: autotuning of launch shapes, CUDA-graph replay and team

@@ -37,7 +37,7 @@ constexpr unsigned long long kKeyMask = (1ull << 33) - 1;
 // ---------------------------------------------------------------------------
 // batch statistics and validation
 // ---------------------------------------------------------------------------
-__global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, int s,
+__global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, int s, int stride,
                              int num_seeds, int d_max, int c, int h_max,
                              const int32_t* __restrict__ dmax_per_read, BatchStats* st) {
     unsigned int my_len = 0;
@@ -64,6 +64,7 @@ __global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, i
             nn = min(nn, (int)m - s + 1);
         }
         if (nn > kMaxSeeds) bad |= kStTooManySeeds;
+        nn *= stride;  // probe slots from here on (stride-k index)
         const int dm = dmax_per_read ? dmax_per_read[r] : d_max;
         if (dm < 0) bad |= kStBadDmax;
         my_len = max(my_len, (unsigned int)m);
@@ -276,6 +277,7 @@ struct FusedArgs {
     unsigned long long* head;
     int d_max, h_max, c, num_seeds;
     int first_seeds;  // non-popular seeds that vote before the first pick (<= 1: Algorithm 1)
+    int stride;       // index stride: probes per seed
     const int32_t* dmax_per_read;
     uint8_t shifts[32];
     int n_shifts;
@@ -648,11 +650,12 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
     const int m = (int)(o1 - o0);
     const uint64_t rb = o0 - a.base0 + kReadPadBases;
     const int s = a.s;
-    int n = 0;
+    int ng = 0;  // seeds
     if (m >= s) {
-        n = a.num_seeds > 0 ? a.num_seeds : m / s;
-        n = min(n, m - s + 1);
+        ng = a.num_seeds > 0 ? a.num_seeds : m / s;
+        ng = min(ng, m - s + 1);
     }
+    const int n = ng * a.stride;  // probe slots (stride-k index: k per seed)
     const int dmax = a.dmax_per_read ? a.dmax_per_read[r] : a.d_max;
     const int c = a.c;
     long long res_loc = -1;
@@ -673,16 +676,24 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
             wm.Xr[w] = rc;
         }
         __syncwarp();
-        // ---- seeds and index probes, one lane per seed ----
+        // ---- seeds and index probes, one lane per probe ----
         unsigned int H = 0;
-        int last_np = -1;  // last non-popular seed (for the seeds-first variant)
+        int last_np = -1;  // last probe after which a pick happens (seeds-first variant)
         for (int i = lane; i < n; i += 32) {
             bool p0 = false;
-            const int o = seed_offset(i, m, s, a.shifts, a.n_shifts, &p0);
+            const int o = probe_offset(i, a.stride, m, s, a.shifts, a.n_shifts, &p0);
             SeedRec rec;
+            rec.pad = 0;
+            if (o < 0) {  // a probe that does not fit in the read
+                rec.flags = 0;
+                rec.offset = 0;
+                rec.fwd_n = rec.rc_n = 0;
+                rec.fwd_ref = rec.rc_ref = 0;
+                wm.seeds[i] = rec;
+                continue;
+            }
             rec.flags = (uint8_t)(kSeedValid | (p0 ? kSeedPass0 : 0));
             rec.offset = (uint16_t)o;
-            rec.pad = 0;
             const uint64_t v = get32(wm.Xf, (uint64_t)o) & kmer_mask(s);
             uint32_t cnt = 0;
             lookup_seed(a.slots, a.T, a.positions, v, s, &rec, &cnt, a.status, &wc.slot_reads);
@@ -691,9 +702,20 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                 rec.flags |= kSeedPopular;
             } else {
                 H += (unsigned int)rec.fwd_n + rec.rc_n;
-                last_np = i;
+                if (a.stride == 1) {  // a probe is a seed
+                    rec.flags |= (uint8_t)(kSeedPick | (p0 ? kSeedCountT : 0));
+                    last_np = i;
+                }
             }
             wm.seeds[i] = rec;
+        }
+        if (a.stride > 1) {  // per seed: its last non-popular probe picks
+            __syncwarp();
+            for (int g = lane; g < ng; g += 32)
+                last_np = max(last_np, mark_seed_group(g, a.stride, n, [&](int i) {
+                                  return &wm.seeds[i].flags;
+                              }));
+            __syncwarp();
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -870,7 +892,8 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                 }
                 SeedRec rec;
                 if (!draining) {
-                    while (i < n && (wm.seeds[i].flags & kSeedPopular)) ++i;
+                    while (i < n && (wm.seeds[i].flags & (kSeedValid | kSeedPopular)) != kSeedValid)
+                        ++i;
                     if (i >= n) break;
                     rec = wm.seeds[i++];
                     any_nonpopular = true;
@@ -903,7 +926,8 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                     nd += __popc(nb);
                 }
                 __syncwarp();
-                if (rec.flags & kSeedPass0) ++t;
+                if (rec.flags & kSeedCountT) ++t;
+                if (!(rec.flags & kSeedPick)) continue;  // more probes of this seed to come
                 // seeds-first variant: the first first_seeds non-popular seeds (all
                 // of them when fewer remain) vote before the first pick; no exit
                 // test can pass before a score
@@ -1254,7 +1278,7 @@ int prepare_batch(const snap_index* idx, Engine* e, const uint8_t* d_reads,
     SNAP_CUDA(cudaMemsetAsync(d_st, 0, sizeof(BatchStats), stream), "stats clear");
     e->launches++;
     k_read_stats<<<grid_cap(e->sms, n, 256), 256, 0, stream>>>(
-        d_offsets, n, idx->s, p->num_seeds, p->max_dist, p->conf_diff, p->max_hits,
+        d_offsets, n, idx->s, idx->stride, p->num_seeds, p->max_dist, p->conf_diff, p->max_hits,
         p->max_dist_per_read, d_st);
     SNAP_CUDA(cudaGetLastError(), "stats launch");
     BatchStats* h_st = static_cast<BatchStats*>(e->pin.p);
@@ -1370,6 +1394,7 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     a.c = p->conf_diff;
     a.num_seeds = p->num_seeds;
     a.first_seeds = p->first_seeds;
+    a.stride = idx->stride;
     a.dmax_per_read = p->max_dist_per_read;
     shift_list(idx->s, a.shifts, &a.n_shifts);
     a.out = d_out;
@@ -1908,7 +1933,7 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
     SNAP_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     SNAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
     k_read_stats<<<grid_cap(sms, n, 256), 256, 0, stream>>>(
-        d_offsets, n, idx->s, p->num_seeds, p->max_dist, p->conf_diff, p->max_hits,
+        d_offsets, n, idx->s, idx->stride, p->num_seeds, p->max_dist, p->conf_diff, p->max_hits,
         p->max_dist_per_read, d_st);
     SNAP_CUDA(cudaGetLastError(), "stats launch");
     BatchStats hs;
@@ -1951,6 +1976,7 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
     a.c = p->conf_diff;
     a.num_seeds = p->num_seeds;
     a.first_seeds = p->first_seeds;
+    a.stride = idx->stride;
     a.dmax_per_read = p->max_dist_per_read;
     shift_list(idx->s, a.shifts, &a.n_shifts);
     a.out = d_out;

@@ -173,6 +173,44 @@ __device__ __forceinline__ int seed_offset(int i, int m, int s, const uint8_t* s
     return -1;
 }
 
+// Probe slot i of a read for an index of windows starting at multiples of
+// `stride` (1 = every window): seed i / stride of the order above, looked up at
+// its offset + i % stride so that an error-free seed meets one indexed window
+// whatever the alignment; -1 when that probe does not fit in the read.
+__device__ __forceinline__ int probe_offset(int i, int stride, int m, int s,
+                                            const uint8_t* shifts, int n_shifts, bool* pass0) {
+    const int g = stride == 1 ? i : i / stride;
+    const int j = i - g * stride;
+    const int o = seed_offset(g, m, s, shifts, n_shifts, pass0);
+    if (o < 0 || o + j + s > m) return -1;
+    return o + j;
+}
+
+// Marks, for the probes of seed g (slots g*stride .. g*stride+stride-1 of
+// flags), the last valid non-popular probe with kSeedPick (the seed's votes are
+// in after it) and, when the seed is of the unshifted pass and none of its
+// valid probes was popular, also kSeedCountT (it counts toward t).  Returns
+// that probe's slot, or -1 when the seed has no non-popular probe.
+template <typename FlagAt>
+__device__ __forceinline__ int mark_seed_group(int g, int stride, int nslots, FlagAt flag_at) {
+    int last = -1;
+    bool all_np = true, p0 = false;
+    for (int j = 0; j < stride; ++j) {
+        const int i = g * stride + j;
+        if (i >= nslots) break;
+        const uint8_t f = *flag_at(i);
+        if (!(f & kSeedValid)) continue;
+        p0 = (f & kSeedPass0) != 0;
+        if (f & kSeedPopular) {
+            all_np = false;
+        } else {
+            last = i;
+        }
+    }
+    if (last >= 0) *flag_at(last) |= (uint8_t)(kSeedPick | ((all_np && p0) ? kSeedCountT : 0));
+    return last;
+}
+
 // ---- bounded edit distance -------------------------------------------------
 // ED(X, T) = min over prefixes T[0..j) of Lev(X, T[0..j)), exact when <= L,
 // else kOver.  X: m bases packed at X (padded); T: n bases packed at Tw from

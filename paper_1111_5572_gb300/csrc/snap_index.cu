@@ -69,11 +69,14 @@ __device__ __forceinline__ void canonical_at(const uint32_t* words, uint64_t l, 
     *orient = v <= rc ? 0 : 1;  // palindromes count as orientation 0
 }
 
-// count pass: insert the canonical key of every window and count its orientation
-__global__ void k_insert(const uint32_t* __restrict__ words, uint64_t npos, int s,
+// count pass: insert the canonical key of every indexed window (starts that are
+// multiples of `stride`, 1 = every window) and count its orientation
+__global__ void k_insert(const uint32_t* __restrict__ words, uint64_t npos, int s, int stride,
                          IndexSlot* slots, uint64_t T, int* status) {
-    for (uint64_t l = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; l < npos;
-         l += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t nidx = (npos + stride - 1) / stride;
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < nidx;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t l = q * (uint64_t)stride;
         uint64_t K;
         int o;
         canonical_at(words, l, s, &K, &o);
@@ -133,11 +136,13 @@ __global__ void k_finalize_slots(IndexSlot* slots, uint64_t T, const uint32_t* s
 
 // fill pass for one orientation: A lists first (orient 0), then B (orient 1),
 // so that B entries land after all A entries of their key
-__global__ void k_fill(const uint32_t* __restrict__ words, uint64_t npos, int s,
+__global__ void k_fill(const uint32_t* __restrict__ words, uint64_t npos, int s, int stride,
                        IndexSlot* slots, uint64_t T, uint32_t* cursor, uint32_t* positions,
                        int which, int* status) {
-    for (uint64_t l = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; l < npos;
-         l += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t nidx = (npos + stride - 1) / stride;
+    for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < nidx;
+         q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t l = q * (uint64_t)stride;
         uint64_t K;
         int o;
         canonical_at(words, l, s, &K, &o);
@@ -189,6 +194,11 @@ using namespace snapgpu;
 
 extern "C" int snap_index_build(const uint8_t* genome_ascii, uint64_t genome_len, int seed_len,
                                 snap_index** out) {
+    return snap_index_build_stride(genome_ascii, genome_len, seed_len, 1, out);
+}
+
+extern "C" int snap_index_build_stride(const uint8_t* genome_ascii, uint64_t genome_len,
+                                       int seed_len, int stride, snap_index** out) {
     clear_error();
     std::lock_guard<std::recursive_mutex> lock(capture_alloc_mutex());
     if (!out) {
@@ -204,6 +214,10 @@ extern "C" int snap_index_build(const uint8_t* genome_ascii, uint64_t genome_len
         set_error("snap_index_build: seed_len %d outside [8, 32]", seed_len);
         return SNAP_E_INVAL;
     }
+    if (stride < 1 || stride > kMaxStride) {
+        set_error("snap_index_build: stride %d outside [1, %d]", stride, kMaxStride);
+        return SNAP_E_INVAL;
+    }
     if (genome_len < (uint64_t)seed_len || genome_len >= (1ull << 32) - (1ull << 16)) {
         set_error("snap_index_build: genome_len %llu outside [seed_len, 2^32 - 2^16)",
                   (unsigned long long)genome_len);
@@ -214,8 +228,10 @@ extern "C" int snap_index_build(const uint8_t* genome_ascii, uint64_t genome_len
     cudaGetDevice(&idx->device);
     idx->G = genome_len;
     idx->s = seed_len;
+    idx->stride = stride;
     const uint64_t npos = genome_len - seed_len + 1;
-    idx->T = ((npos + npos / 2 + 64) + kBucketSlots - 1) / kBucketSlots * kBucketSlots;  // load <= 2/3
+    const uint64_t nidx = (npos + stride - 1) / stride;  // indexed windows
+    idx->T = ((nidx + nidx / 2 + 64) + kBucketSlots - 1) / kBucketSlots * kBucketSlots;  // load <= 2/3
     idx->genome_words_n = (genome_len + 15) / 16 + 8;
 
     uint8_t* d_ascii = nullptr;
@@ -270,8 +286,8 @@ extern "C" int snap_index_build(const uint8_t* genome_ascii, uint64_t genome_len
 
     TRY(cudaMalloc(&idx->slots, idx->T * sizeof(IndexSlot)), "table alloc");
     k_init_slots<<<grid_for(idx->T, 256), 256, 0, st>>>(idx->slots, idx->T);
-    k_insert<<<grid_for(npos, 256), 256, 0, st>>>(idx->genome_words, npos, seed_len, idx->slots,
-                                                  idx->T, d_status);
+    k_insert<<<grid_for(nidx, 256), 256, 0, st>>>(idx->genome_words, npos, seed_len, stride,
+                                                  idx->slots, idx->T, d_status);
     TRY(cudaGetLastError(), "insert launch");
     TRY(cudaMalloc(&d_cursor, idx->T * sizeof(uint32_t)), "cursor alloc");
     k_list_lengths<<<grid_for(idx->T, 256), 256, 0, st>>>(idx->slots, idx->T, d_cursor,
@@ -293,9 +309,9 @@ extern "C" int snap_index_build(const uint8_t* genome_ascii, uint64_t genome_len
     idx->n_positions = hc[1];
     TRY(cudaMalloc(&idx->positions, (idx->n_positions + 4) * sizeof(uint32_t)), "list alloc");
     for (int which = 0; which < 2; ++which) {
-        k_fill<<<grid_for(npos, 256), 256, 0, st>>>(idx->genome_words, npos, seed_len, idx->slots,
-                                                    idx->T, d_cursor, idx->positions, which,
-                                                    d_status);
+        k_fill<<<grid_for(nidx, 256), 256, 0, st>>>(idx->genome_words, npos, seed_len, stride,
+                                                    idx->slots, idx->T, d_cursor, idx->positions,
+                                                    which, d_status);
     }
     TRY(cudaGetLastError(), "fill launch");
     TRY(cudaMemcpyAsync(&hstatus, d_status, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
@@ -339,7 +355,7 @@ extern "C" int snap_index_info_get(const snap_index* idx, snap_index_info* out) 
     }
     out->genome_len = idx->G;
     out->seed_len = idx->s;
-    out->reserved = 0;
+    out->stride = idx->stride;
     out->table_slots = idx->T;
     out->distinct_seeds = idx->distinct;
     out->list_entries = idx->n_positions;

@@ -17,6 +17,7 @@ namespace snapgpu {
 constexpr unsigned long long kEmptyKey = ~0ull;  // never a canonical s-mer (see snap_index.cu)
 constexpr uint32_t kListMax = 65534;             // longest stored position list; max h_max
 constexpr int kMaxSeeds = 2047;                  // seeds per read (11-bit vote counter)
+constexpr int kMaxStride = 16;                   // stride-k index: largest k
 constexpr int kMaxReadLen = 65535;
 constexpr int kReadPadBases = 32;                // packed read stream starts 32 bases in
 constexpr uint32_t kMaxTableSlots = 1u << 20;    // per-read candidate table (20-bit slot id)
@@ -64,7 +65,10 @@ struct __align__(16) SeedRec {
 };
 static_assert(sizeof(SeedRec) == 16, "seed record is 16 bytes");
 enum : uint8_t { kSeedPopular = 1, kSeedPass0 = 2, kSeedFwdInline = 4, kSeedRcInline = 8,
-                 kSeedValid = 16 };
+                 kSeedValid = 16,
+                 kSeedPick = 32,     // pick and score after this probe's votes (its seed's last
+                                     // non-popular probe)
+                 kSeedCountT = 64 };  // this probe's seed counts toward t
 
 // Candidate table slot of one read (16 bytes): key = 2p + strand.
 struct __align__(16) CandSlot {
@@ -121,6 +125,7 @@ struct snap_index {
     int device = 0;
     uint64_t G = 0;
     int s = 0;
+    int stride = 1;                    // indexed windows start at multiples of this
     uint32_t* genome_words = nullptr;  // 2-bit packed genome, padded
     uint64_t genome_words_n = 0;
     snapgpu::IndexSlot* slots = nullptr;

@@ -54,6 +54,7 @@ struct LightArgs {
     uint64_t n;
     int d_max, h_max, c, num_seeds;
     int first_seeds;
+    int stride;  // index stride: probes per seed
     const int32_t* dmax_per_read;
     uint8_t shifts[32];
     int n_shifts;
@@ -87,11 +88,12 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
         const uint64_t o0 = a.offsets[r];
         const int m = (int)(a.offsets[r + 1] - o0);
         const int s = a.s;
-        int n = 0;
+        int ng = 0;  // seeds
         if (m >= s) {
-            n = a.num_seeds > 0 ? a.num_seeds : m / s;
-            n = min(n, m - s + 1);
+            ng = a.num_seeds > 0 ? a.num_seeds : m / s;
+            ng = min(ng, m - s + 1);
         }
+        const int n = ng * a.stride;  // probe slots (stride-k index: k per seed)
         const int dmax = a.dmax_per_read ? a.dmax_per_read[r] : a.d_max;
         const int c = a.c;
         bool heavy = m > kLightMaxM || n > kLightMaxSeeds || dmax + c - 1 > kLightMaxL;
@@ -125,11 +127,19 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
             int last_np = -1;  // last non-popular seed (seeds-first variant)
             for (int i = 0; i < n; ++i) {
                 bool p0 = false;
-                const int o = seed_offset(i, m, s, a.shifts, a.n_shifts, &p0);
+                const int o = probe_offset(i, a.stride, m, s, a.shifts, a.n_shifts, &p0);
                 SeedRec rec;
+                rec.pad = 0;
+                if (o < 0) {  // a probe that does not fit in the read
+                    rec.flags = 0;
+                    rec.offset = 0;
+                    rec.fwd_n = rec.rc_n = 0;
+                    rec.fwd_ref = rec.rc_ref = 0;
+                    seeds[i] = rec;
+                    continue;
+                }
                 rec.flags = (uint8_t)(kSeedValid | (p0 ? kSeedPass0 : 0));
                 rec.offset = (uint16_t)o;
-                rec.pad = 0;
                 const uint64_t v = col32(Xf, o, st) & kmer_mask(s);
                 uint32_t cnt = 0;
                 lookup_seed(a.slots, a.T, a.positions, v, s, &rec, &cnt, a.status, &c_slots);
@@ -138,10 +148,18 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                     rec.flags |= kSeedPopular;
                 } else {
                     H += (unsigned)rec.fwd_n + rec.rc_n;
-                    last_np = i;
+                    if (a.stride == 1) {  // a probe is a seed
+                        rec.flags |= (uint8_t)(kSeedPick | (p0 ? kSeedCountT : 0));
+                        last_np = i;
+                    }
                 }
                 seeds[i] = rec;
             }
+            if (a.stride > 1)  // per seed: its last non-popular probe picks
+                for (int g = 0; g < ng; ++g)
+                    last_np = max(last_np, mark_seed_group(g, a.stride, n, [&](int i) {
+                                      return &seeds[i].flags;
+                                  }));
             heavy = H > (unsigned)kLightMaxCands;
             if (!heavy) {
                 unsigned long long ckey[kLightMaxCands];
@@ -157,7 +175,9 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                 int i = 0;
                 for (;;) {
                     if (!draining) {
-                        while (i < n && (seeds[i].flags & kSeedPopular)) ++i;
+                        while (i < n &&
+                               (seeds[i].flags & (kSeedValid | kSeedPopular)) != kSeedValid)
+                            ++i;
                         if (i >= n) break;
                         const SeedRec rec = seeds[i++];
                         any_nonpopular = true;
@@ -188,7 +208,8 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                             }
                             ++cvotes[q];
                         }
-                        if (rec.flags & kSeedPass0) ++t;
+                        if (rec.flags & kSeedCountT) ++t;
+                        if (!(rec.flags & kSeedPick)) continue;  // more probes of this seed
                         // seeds-first variant: no pick before first_seeds non-popular
                         // seeds (or all of them) have voted
                         if (++voted < a.first_seeds && i <= last_np) continue;
@@ -330,6 +351,7 @@ int launch_light(const snap_index* idx, Engine* e, const uint64_t* d_offsets, ui
     a.c = p->conf_diff;
     a.num_seeds = p->num_seeds;
     a.first_seeds = p->first_seeds;
+    a.stride = idx->stride;
     a.dmax_per_read = p->max_dist_per_read;
     shift_list(idx->s, a.shifts, &a.n_shifts);
     a.out = d_out;

@@ -45,6 +45,7 @@ struct PlainArgs {
     int nmax;  // seed slots per read
     int d_max, h_max, c, num_seeds;
     int first_seeds;  // seeds-first variant (<= 1: Algorithm 1)
+    int stride;       // index stride: probes per seed
     const int32_t* dmax_per_read;
     uint8_t shifts[32];
     int n_shifts;
@@ -65,10 +66,16 @@ struct PlainArgs {
     int wx, wt, lv_ints, warp_words;
 };
 
-__device__ __forceinline__ int read_seeds(const PlainArgs& a, int m) {
+// seeds of a read of length m
+__device__ __forceinline__ int read_seed_groups(const PlainArgs& a, int m) {
     if (m < a.s) return 0;
     int nn = a.num_seeds > 0 ? a.num_seeds : m / a.s;
     return min(nn, m - a.s + 1);
+}
+
+// probe slots of a read (stride-k index: k probes per seed)
+__device__ __forceinline__ int read_seeds(const PlainArgs& a, int m) {
+    return read_seed_groups(a, m) * a.stride;
 }
 
 __device__ __forceinline__ void add_counter(unsigned long long* dst, unsigned long long v) {
@@ -100,9 +107,9 @@ __global__ void k_plain_probe(PlainArgs a) {
         rec.offset = 0;
         rec.flags = 0;
         rec.pad = 0;
-        if (i < nn) {
-            bool p0 = false;
-            const int o = seed_offset(i, m, a.s, a.shifts, a.n_shifts, &p0);
+        bool p0 = false;
+        const int o = i < nn ? probe_offset(i, a.stride, m, a.s, a.shifts, a.n_shifts, &p0) : -1;
+        if (o >= 0) {
             rec.flags = (uint8_t)(kSeedValid | (p0 ? kSeedPass0 : 0));
             rec.offset = (uint16_t)o;
             const uint64_t rb = o0 - a.base0 + kReadPadBases;
@@ -349,18 +356,23 @@ __global__ void k_plain_replay(PlainArgs a) {
                     }
                 }
             };
-            // last non-popular seed, for the seeds-first variant
+            // per seed, the probe after which a pick happens (its last non-popular
+            // one), and the last such probe (seeds-first variant)
             int last_np = -1;
-            for (int i = lane; i < nn; i += 32)
-                if (!(a.seeds[r * a.nmax + i].flags & kSeedPopular)) last_np = i;
+            const int ng = read_seed_groups(a, m);
+            for (int g = lane; g < ng; g += 32)
+                last_np = max(last_np, mark_seed_group(g, a.stride, nn, [&](int i) {
+                                  return &a.seeds[r * a.nmax + i].flags;
+                              }));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
                 last_np = max(last_np, __shfl_xor_sync(kFull, last_np, o));
+            __syncwarp();
             int voted = 0;
             uint64_t cur = base;
             for (int i = 0; i < nn; ++i) {
                 const SeedRec rec = a.seeds[r * a.nmax + i];
-                if (rec.flags & kSeedPopular) continue;
+                if ((rec.flags & (kSeedValid | kSeedPopular)) != kSeedValid) continue;
                 any_nonpopular = true;
                 const int tot = (int)rec.fwd_n + rec.rc_n;
                 for (int j = lane; j < tot; j += 32) {
@@ -369,7 +381,8 @@ __global__ void k_plain_replay(PlainArgs a) {
                 }
                 cur += tot;
                 __syncwarp();
-                if (rec.flags & kSeedPass0) ++t;
+                if (rec.flags & kSeedCountT) ++t;
+                if (!(rec.flags & kSeedPick)) continue;  // more probes of this seed to come
                 if (++voted < a.first_seeds && i < last_np) continue;  // seeds-first
                 const unsigned long long pk = cap ? pick() : 0ull;
                 if (pk) score(pk);
@@ -434,6 +447,7 @@ int align_plain(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uin
     a.c = p->conf_diff;
     a.num_seeds = p->num_seeds;
     a.first_seeds = p->first_seeds;
+    a.stride = idx->stride;
     a.dmax_per_read = p->max_dist_per_read;
     shift_list(idx->s, a.shifts, &a.n_shifts);
     a.out = d_out;

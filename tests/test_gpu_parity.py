@@ -221,6 +221,34 @@ def test_seeds_first_variant(snap):
                 assert_same(got, ref, f"{name} first_seeds={k} plain={plain}")
 
 
+@pytest.mark.parametrize("stride", [2, 3])
+def test_stride_k_index(snap, stride):
+    # stride-k index (only windows at multiples of k; each seed probed at k offsets):
+    # both forms against the oracle with the same stride, on short reads (C2 recipe),
+    # uneven lengths with per-read limits (C3 recipe: probes near the read end are cut)
+    # and the repeat-dense C5 recipe, plus the error-free phase case of the oracle pins
+    for name, G, n in (("C2", 3_000_000, 20_000), ("C3", 4_000_000, 3000),
+                       ("C5", 10_000_000, 20_000)):
+        w = synth.CONFIGS[name].scaled(G=G, n_reads=n)
+        g, _ = w.make_genome()
+        rd = w.make_reads(g)
+        dpr = w.max_dist_per_read(rd.lengths())
+        gi = snap.Index(g, w.seed_len, stride=stride)
+        info = gi.info()
+        assert info["stride"] == stride
+        ref, st = oracle.Index(g, w.seed_len, stride=stride).align(
+            rd.bases, rd.offsets, max_dist_per_read=dpr, threads=4, **w.params())
+        for plain in (False, True):
+            got = gi.align(rd.bases, rd.offsets, max_dist_per_read=dpr, plain=plain,
+                           **w.params())
+            assert_same(got, ref, f"{name} stride={stride} plain={plain}")
+        assert gi.last_call_stats()["seeds"] == st.seeds_looked_up
+    g = np.frombuffer(b"ACGT", dtype=np.uint8)[np.random.default_rng(3).integers(0, 4, 100)]
+    for bad in (0, 17):
+        with pytest.raises(snap.SnapError):
+            snap.Index(np.tile(g, 100), 20, stride=bad)
+
+
 def test_autotune_and_graph_replay_keep_results(snap):
     # launch shapes and graph replay must never change a result: compare against the
     # untuned, ungraphed run on several batch sizes, through the graph update path
