@@ -73,6 +73,10 @@ __device__ __forceinline__ uint64_t col32(const uint32_t* col, int i, int st) {
     return ((uint64_t)__funnelshift_r(w1, w2, sh) << 32) | __funnelshift_r(w0, w1, sh);
 }
 
+// VARIANT: the index has a stride > 1 or first_seeds > 1 (probe slots grouped
+// per seed, picks deferred); without it a probe is a seed and every non-popular
+// one picks, which keeps the common case's registers free.
+template <bool VARIANT>
 __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     const int tid = threadIdx.x;
@@ -93,7 +97,8 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
             ng = a.num_seeds > 0 ? a.num_seeds : m / s;
             ng = min(ng, m - s + 1);
         }
-        const int n = ng * a.stride;  // probe slots (stride-k index: k per seed)
+        const int stride = VARIANT ? a.stride : 1;
+        const int n = ng * stride;  // probe slots (stride-k index: k per seed)
         const int dmax = a.dmax_per_read ? a.dmax_per_read[r] : a.d_max;
         const int c = a.c;
         bool heavy = m > kLightMaxM || n > kLightMaxSeeds || dmax + c - 1 > kLightMaxL;
@@ -127,7 +132,8 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
             int last_np = -1;  // last non-popular seed (seeds-first variant)
             for (int i = 0; i < n; ++i) {
                 bool p0 = false;
-                const int o = probe_offset(i, a.stride, m, s, a.shifts, a.n_shifts, &p0);
+                const int o = VARIANT ? probe_offset(i, stride, m, s, a.shifts, a.n_shifts, &p0)
+                                      : seed_offset(i, m, s, a.shifts, a.n_shifts, &p0);
                 SeedRec rec;
                 rec.pad = 0;
                 if (o < 0) {  // a probe that does not fit in the read
@@ -148,14 +154,14 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                     rec.flags |= kSeedPopular;
                 } else {
                     H += (unsigned)rec.fwd_n + rec.rc_n;
-                    if (a.stride == 1) {  // a probe is a seed
+                    if (stride == 1) {  // a probe is a seed
                         rec.flags |= (uint8_t)(kSeedPick | (p0 ? kSeedCountT : 0));
-                        last_np = i;
+                        if (VARIANT) last_np = i;
                     }
                 }
                 seeds[i] = rec;
             }
-            if (a.stride > 1)  // per seed: its last non-popular probe picks
+            if (VARIANT && stride > 1)  // per seed: its last non-popular probe picks
                 for (int g = 0; g < ng; ++g)
                     last_np = max(last_np, mark_seed_group(g, a.stride, n, [&](int i) {
                                       return &seeds[i].flags;
@@ -209,10 +215,12 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                             ++cvotes[q];
                         }
                         if (rec.flags & kSeedCountT) ++t;
-                        if (!(rec.flags & kSeedPick)) continue;  // more probes of this seed
-                        // seeds-first variant: no pick before first_seeds non-popular
-                        // seeds (or all of them) have voted
-                        if (++voted < a.first_seeds && i <= last_np) continue;
+                        if (VARIANT) {
+                            if (!(rec.flags & kSeedPick)) continue;  // more probes of this seed
+                            // seeds-first variant: no pick before first_seeds non-popular
+                            // seeds (or all of them) have voted
+                            if (++voted < a.first_seeds && i <= last_np) continue;
+                        }
                     }
                     // most-voted unscored candidate, ties to the smaller key
                     int pick = -1;
@@ -325,7 +333,9 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
 
 // Shared-memory limit of the thread-per-read kernel, set once (before any capture).
 int light_prepare() {
-    return raise_smem_limit((const void*)k_align_light, (size_t)kLightWords * 256 * 4);
+    int rc = raise_smem_limit((const void*)k_align_light<false>, (size_t)kLightWords * 256 * 4);
+    if (rc) return rc;
+    return raise_smem_limit((const void*)k_align_light<true>, (size_t)kLightWords * 256 * 4);
 }
 
 // Launch the thread-per-read bucket over all n reads; reads it does not take
@@ -365,7 +375,10 @@ int launch_light(const snap_index* idx, Engine* e, const uint64_t* d_offsets, ui
     SNAP_CUDA(cudaMemsetAsync(heavy_count, 0, sizeof(unsigned long long), stream), "clear");
     const uint64_t blocks = (n + threads - 1) / threads;
     e->launches++;
-    k_align_light<<<(unsigned)blocks, threads, smem, stream>>>(a);
+    if (a.stride > 1 || a.first_seeds > 1)
+        k_align_light<true><<<(unsigned)blocks, threads, smem, stream>>>(a);
+    else
+        k_align_light<false><<<(unsigned)blocks, threads, smem, stream>>>(a);
     SNAP_CUDA(cudaGetLastError(), "light launch");
     return SNAP_OK;
 }
