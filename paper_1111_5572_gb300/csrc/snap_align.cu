@@ -643,7 +643,10 @@ __device__ __forceinline__ int candidate_distance(const FusedArgs& a, const Warp
     return d;
 }
 
-template <int LVD, bool TEAM>
+// VARIANT: the index has a stride > 1 or first_seeds > 1 (probe slots grouped
+// per seed, picks deferred); without it a probe is a seed and every non-popular
+// one picks.
+template <int LVD, bool TEAM, bool VARIANT>
 __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem& wm, uint64_t r,
                                                int lane, WarpCounters& wc) {
     const uint64_t o0 = a.offsets[r], o1 = a.offsets[r + 1];
@@ -655,7 +658,8 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
         ng = a.num_seeds > 0 ? a.num_seeds : m / s;
         ng = min(ng, m - s + 1);
     }
-    const int n = ng * a.stride;  // probe slots (stride-k index: k per seed)
+    const int stride = VARIANT ? a.stride : 1;
+    const int n = ng * stride;  // probe slots (stride-k index: k per seed)
     const int dmax = a.dmax_per_read ? a.dmax_per_read[r] : a.d_max;
     const int c = a.c;
     long long res_loc = -1;
@@ -681,10 +685,11 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
         int last_np = -1;  // last probe after which a pick happens (seeds-first variant)
         for (int i = lane; i < n; i += 32) {
             bool p0 = false;
-            const int o = probe_offset(i, a.stride, m, s, a.shifts, a.n_shifts, &p0);
+            const int o = VARIANT ? probe_offset(i, stride, m, s, a.shifts, a.n_shifts, &p0)
+                                  : seed_offset(i, m, s, a.shifts, a.n_shifts, &p0);
             SeedRec rec;
             rec.pad = 0;
-            if (o < 0) {  // a probe that does not fit in the read
+            if (VARIANT && o < 0) {  // a probe that does not fit in the read
                 rec.flags = 0;
                 rec.offset = 0;
                 rec.fwd_n = rec.rc_n = 0;
@@ -702,17 +707,17 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                 rec.flags |= kSeedPopular;
             } else {
                 H += (unsigned int)rec.fwd_n + rec.rc_n;
-                if (a.stride == 1) {  // a probe is a seed
+                if (stride == 1) {  // a probe is a seed
                     rec.flags |= (uint8_t)(kSeedPick | (p0 ? kSeedCountT : 0));
-                    last_np = i;
+                    if (VARIANT) last_np = i;
                 }
             }
             wm.seeds[i] = rec;
         }
-        if (a.stride > 1) {  // per seed: its last non-popular probe picks
+        if (VARIANT && stride > 1) {  // per seed: its last non-popular probe picks
             __syncwarp();
             for (int g = lane; g < ng; g += 32)
-                last_np = max(last_np, mark_seed_group(g, a.stride, n, [&](int i) {
+                last_np = max(last_np, mark_seed_group(g, stride, n, [&](int i) {
                                   return &wm.seeds[i].flags;
                               }));
             __syncwarp();
@@ -720,7 +725,7 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             H += __shfl_xor_sync(kFull, H, o);
-            last_np = max(last_np, __shfl_xor_sync(kFull, last_np, o));
+            if (VARIANT) last_np = max(last_np, __shfl_xor_sync(kFull, last_np, o));
         }
         // ---- candidate table: shared memory when it fits, else this warp's global one ----
         uint32_t cap = 64;
@@ -892,7 +897,9 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                 }
                 SeedRec rec;
                 if (!draining) {
-                    while (i < n && (wm.seeds[i].flags & (kSeedValid | kSeedPopular)) != kSeedValid)
+                    while (i < n && (VARIANT ? (wm.seeds[i].flags & (kSeedValid | kSeedPopular)) !=
+                                                   kSeedValid
+                                             : (wm.seeds[i].flags & kSeedPopular) != 0))
                         ++i;
                     if (i >= n) break;
                     rec = wm.seeds[i++];
@@ -927,11 +934,13 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                 }
                 __syncwarp();
                 if (rec.flags & kSeedCountT) ++t;
-                if (!(rec.flags & kSeedPick)) continue;  // more probes of this seed to come
-                // seeds-first variant: the first first_seeds non-popular seeds (all
-                // of them when fewer remain) vote before the first pick; no exit
-                // test can pass before a score
-                if (++voted < a.first_seeds && i <= last_np) continue;
+                if constexpr (VARIANT) {
+                    if (!(rec.flags & kSeedPick)) continue;  // more probes of this seed to come
+                    // seeds-first variant: the first first_seeds non-popular seeds (all
+                    // of them when fewer remain) vote before the first pick; no exit
+                    // test can pass before a score
+                    if (++voted < a.first_seeds && i <= last_np) continue;
+                }
                 }
                 const unsigned long long pk = table_pick(tab, dense, nd, lane);
                 if (pk) {
@@ -978,7 +987,7 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
     __syncwarp();
 }
 
-template <int LVD>
+template <int LVD, bool VARIANT>
 __global__ void __launch_bounds__(256, 4) k_align_fused(FusedArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1010,13 +1019,14 @@ __global__ void __launch_bounds__(256, 4) k_align_fused(FusedArgs a) {
         it = __shfl_sync(kFull, it, 0);
         if (it >= n_items) break;
         const uint64_t r = a.order ? a.order[it] : it;
-        align_one_read<LVD, false>(a, wm, r, lane, wc);
+        align_one_read<LVD, false, VARIANT>(a, wm, r, lane, wc);
     }
     flush_counters(a.ctr, wc);
 }
 
 // Team mode (see team_distance): one read per block at a time, kTeamWarps warps;
 // warp 0 leads, the shared-memory layout is that of one warp plus the job words.
+template <bool VARIANT>
 __global__ void __launch_bounds__(kTeamWarps * 32) k_align_team(FusedArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1052,7 +1062,7 @@ __global__ void __launch_bounds__(kTeamWarps * 32) k_align_team(FusedArgs a) {
         it = __shfl_sync(kFull, it, 0);
         if (it >= n_items) break;
         const uint64_t r = a.order ? a.order[it] : it;
-        align_one_read<0, true>(a, wm, r, lane, wc);
+        align_one_read<0, true, VARIANT>(a, wm, r, lane, wc);
     }
     if (lane == 0) wm.job[0] = kJobExit;
     __syncthreads();  // releases the helpers
@@ -1064,10 +1074,24 @@ using FusedKernel = void (*)(FusedArgs);
 // The kernel variant for a batch whose largest limit is Lmax: one or two
 // register diagonals per lane when they cover [-Lmax, Lmax], else shared memory,
 // with the q-gram bound when some read of the class can use it (qmaps).
-static FusedKernel fused_kernel_for(int Lmax, bool qmaps = false) {
-    if (Lmax <= 15) return k_align_fused<1>;
-    if (Lmax <= 31) return k_align_fused<2>;
-    return qmaps ? k_align_fused<-1> : k_align_fused<0>;
+static FusedKernel fused_kernel_for(int Lmax, bool qmaps, bool variant) {
+    if (variant) {
+        if (Lmax <= 15) return k_align_fused<1, true>;
+        if (Lmax <= 31) return k_align_fused<2, true>;
+        return qmaps ? k_align_fused<-1, true> : k_align_fused<0, true>;
+    }
+    if (Lmax <= 15) return k_align_fused<1, false>;
+    if (Lmax <= 31) return k_align_fused<2, false>;
+    return qmaps ? k_align_fused<-1, false> : k_align_fused<0, false>;
+}
+
+// The parameters that need the per-seed pick marks (see align_one_read).
+static bool param_variant(const snap_index* idx, const snap_params* p) {
+    return idx->stride > 1 || p->first_seeds > 1;
+}
+
+static bool is_team_kernel(FusedKernel k) {
+    return k == k_align_team<false> || k == k_align_team<true>;
 }
 
 // ---------------------------------------------------------------------------
@@ -1452,7 +1476,9 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     bool qmaps = false;
     for (int L = kQMinL; L <= Lmax && !qmaps; ++L)
         qmaps = use_qfilter(std::min(mmax, L * L / 8 - L), L);
-    const FusedKernel kfn = team ? k_align_team : fused_kernel_for(Lmax, qmaps);
+    const bool variant = param_variant(idx, p);
+    const FusedKernel kfn = team ? (variant ? k_align_team<true> : k_align_team<false>)
+                                 : fused_kernel_for(Lmax, qmaps, variant);
     const int threads = team ? kTeamWarps * 32 : warps * 32;
     if ((rc = raise_smem_limit((const void*)kfn, smem))) return rc;
     int per_sm = 0;
@@ -1654,7 +1680,7 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
             break;
         }
     e->last_team = 0;
-    for (int q = 0; q < kClasses; ++q) e->last_team += plan.use[q] && plan.kfn[q] == k_align_team;
+    for (int q = 0; q < kClasses; ++q) e->last_team += plan.use[q] && is_team_kernel(plan.kfn[q]);
     e->last_graph = 0;
     if (e->use_graphs && stream != nullptr && stream != cudaStreamLegacy &&
         stream != cudaStreamPerThread) {
@@ -2010,7 +2036,7 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
         set_error("%s: read length %d needs too much shared memory", where, mmax);
         return SNAP_E_INVAL;
     }
-    const FusedKernel kfn = fused_kernel_for(Lmax);
+    const FusedKernel kfn = fused_kernel_for(Lmax, false, param_variant(idx, p));
     if ((rc = raise_smem_limit((const void*)kfn, (size_t)(int)smem))) return rc;
     int per_sm = 0;
     SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem),
