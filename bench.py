@@ -99,6 +99,20 @@ def _dist():
     return ws, rank, local
 
 
+def job_throughput(total_s: float, reads_per_rank: int, steps: int, ws: int, device=None):
+    """Whole-job reads/s of N replicas (reads are independent; each rank aligns its own
+    reads with its own index copy, no collective on the data path): every rank's
+    timed seconds are reduced to the slowest rank's, and all ranks' reads count.
+    Returns (reads/s, the slowest rank's seconds)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    return reads_per_rank * ws * steps / total_s, total_s
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
 
@@ -350,12 +364,7 @@ def run_ours(args):
         return step_ms, stats, clk.summary(), wall
 
     step_ms, stats, clocks, wall = timed(plain, args.steps, args.warmup)
-    total_s = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = n * ws * args.steps / total_s
+    value, total_s = job_throughput(sum(step_ms) / 1e3, n, args.steps, ws, dev)
     ms_per_step = total_s * 1e3 / args.steps
     launches = int(sum(s["kernel_launches"] for s in stats))
     got = d_out.cpu().numpy().view(snap.RESULT_DTYPE).reshape(-1)
