@@ -170,12 +170,37 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _strip_comments(src: str) -> str:
+    """C/C++ source without comments and blank runs (string and char literals kept)."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            while i < n and src[i] != "\n":
+                i += 1
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def _kernel_source_hash():
+    """Hash of the kernel sources' code (comments and layout ignored): a committed ncu
+    capture stays valid across comment edits, and no longer once any code changed."""
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_1111_5572_gb300", "csrc")
     for fn in sorted(os.listdir(cs)):
-        with open(os.path.join(cs, fn), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(cs, fn), encoding="utf-8") as f:
+            h.update(fn.encode() + b"\0" + _strip_comments(f.read()).encode())
     return h.hexdigest()[:16]
 
 

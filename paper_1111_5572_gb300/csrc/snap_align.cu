@@ -2,17 +2,20 @@
 // and the persistent warp-per-read kernel that runs Algorithm 1 ("SNAP
 // alignment algorithm") literally for each read it pulls from a device queue.
 //
-// Per read, one warp:
+// Per read, one warp (or, in team mode, one block whose first warp does this):
 //   * packs the read and its reverse complement (2 bits per base) into shared
 //     memory;
 //   * cuts the seeds in the order of item 3 after Algorithm 1 and probes the
-//     index for all of them at once (one lane per seed);
+//     index for all of them at once (one lane per probe: a seed has one probe,
+//     or k of them on a stride-k index);
 //   * walks the seeds in order: adds the votes SeedsHitting[p] of a seed with
 //     at most h_max entries (lanes over list entries, a shared-memory hash
 //     table keyed by (strand, p)), picks the most-voted unscored candidate
 //     (warp arg-max, ties to the smaller key), computes d_limit, scores it with
-//     the warp's Landau-Vishkin edit distance, keeps d_best / d_second over
-//     32-base buckets (item 1 after Algorithm 1), and takes the early exits;
+//     the Landau-Vishkin edit distance (behind the q-gram bound for large
+//     limits), keeps d_best / d_second over 32-base buckets (item 1 after
+//     Algorithm 1), and takes the early exits; after the Baeza-Yates test the
+//     remaining candidates are scored 32 at a time (the parallel drain);
 //   * classifies the read (single / multiple / not found).
 // Readings where the paper is silent (all shared with the oracle's statement
 // of them): votes from revcomp(seed) go to strand 1 at p = l - (m - o - s);
