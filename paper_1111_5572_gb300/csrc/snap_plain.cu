@@ -1,7 +1,8 @@
 // snap_plain.cu — the plain form of the alignment path: one kernel launch per
 // stage over the whole batch, no persistent queue, no graph.  It computes the
 // same results as the batched form by another route:
-//   1. probe:      one thread per (read, seed) looks the seed up in the index;
+//   1. probe:      one thread per (read, probe) looks the seed up in the index
+//                  (a seed is one probe, or k consecutive ones on a stride-k index);
 //   2. scan:       per-read hit counts -> offsets (host reads the total);
 //   3. candidates: one warp per read gathers the votes of its non-popular seeds
 //                  into a per-read table (distinct (strand, p) keys) and records,
@@ -9,7 +10,8 @@
 //   4. distance:   one warp per candidate computes its edit distance once, at the
 //                  largest limit the read can use, L0 = d_max + c - 1;
 //   5. replay:     one warp per read replays Algorithm 1 seed by seed from the
-//                  recorded votes, with ED(L) = (d0 <= L ? d0 : over).
+//                  recorded votes, with ED(L) = (d0 <= L ? d0 : over) (and the
+//                  seeds-first variant's deferred first pick).
 // Step 5 gives Algorithm 1's result because the pick order depends only on the
 // votes and on which candidates were scored, never on distances, and every
 // limit the algorithm uses is at most L0, so the distance at any limit follows
