@@ -41,3 +41,19 @@ def test_accuracy_with_no_confident_reads():
     got["cls"] = [0, 2]
     a = bench.accuracy(got, rd)
     assert a["aligned_pct"] == 0.0 and a["error_pct"] == 0.0
+
+
+def test_cpu_oracle_sample_reports_all_cores_and_one_core():
+    # the bench's CPU baseline: the oracle as it stands, timed on a bounded sample on
+    # all host cores and on one; the sample's results are the oracle's own
+    import oracle
+    w = synth.CONFIGS["C1"].scaled(G=300_000, n_reads=3000)
+    g, _ = w.make_genome()
+    rd = w.make_reads(g)
+    cb, sample, res = bench.cpu_oracle_sample(w, g, rd, None, target_s=0.2)
+    assert cb["kind"] == "oracle" and cb["cores"] == (os.cpu_count() or 1)
+    assert cb["value"] > 0 and cb["single_core"]["value"] > 0
+    assert 200 <= cb["single_core"]["reads"] <= len(sample)
+    ref, _ = oracle.Index(g, w.seed_len).align(rd.bases, rd.offsets, **w.params())
+    for f in ("location", "edit_distance", "strand", "cls"):
+        assert np.array_equal(res[f], ref[f][:len(sample)])
