@@ -7,7 +7,7 @@
 //
 // What it computes, and the passage each part follows:
 //   * index: the "Hash Index" subsection — every overlapping s-mer of the genome
-//     (sliding window of one base), with lookups of both a seed and its reverse
+//     (sliding window of one base; or every k-th, R9), with lookups of both a seed and its reverse
 //     complement, as "populate the index with both forward and reverse
 //     complement versions" (item 2 of the list after Algorithm 1) asks.  Here it
 //     is a sorted array of (s-mer, position) pairs searched with binary search.
