@@ -291,6 +291,8 @@ struct FusedArgs {
     uint32_t gcap;
     SeedRec* gseeds;  // per-warp seed records (seed_cap each) when not in shared memory
     uint32_t* gqbits; // per-warp q-gram bitmaps (2 x kQWords) for large limits, or NULL
+    const SeedRec* hseeds;   // probe records of reads handed over by the short-read
+    const uint8_t* hprobed;  // bucket (kLightBucketMaxSeeds per read), flagged per read
     int* status;
     DevCounters* ctr;
     // per-warp shared-memory layout, in 32-bit words; every section offset is a
@@ -686,7 +688,19 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
         // ---- seeds and index probes, one lane per probe ----
         unsigned int H = 0;
         int last_np = -1;  // last probe after which a pick happens (seeds-first variant)
-        for (int i = lane; i < n; i += 32) {
+        // a read the short-read bucket probed before handing it over: its records
+        const bool reuse = a.hprobed != nullptr && a.hprobed[r] != 0;
+        if (reuse) {
+            for (int i = lane; i < n; i += 32) {
+                const SeedRec rec = a.hseeds[r * kLightBucketMaxSeeds + i];
+                wm.seeds[i] = rec;
+                if ((rec.flags & (kSeedValid | kSeedPopular)) == kSeedValid) {
+                    H += (unsigned int)rec.fwd_n + rec.rc_n;
+                    if (VARIANT && (rec.flags & kSeedPick)) last_np = i;
+                }
+            }
+        }
+        for (int i = reuse ? n : lane; i < n; i += 32) {
             bool p0 = false;
             const int o = VARIANT ? probe_offset(i, stride, m, s, a.shifts, a.n_shifts, &p0)
                                   : seed_offset(i, m, s, a.shifts, a.n_shifts, &p0);
@@ -717,7 +731,7 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
             }
             wm.seeds[i] = rec;
         }
-        if (VARIANT && stride > 1) {  // per seed: its last non-popular probe picks
+        if (VARIANT && stride > 1 && !reuse) {  // per seed: its last non-popular probe picks
             __syncwarp();
             for (int g = lane; g < ng; g += 32)
                 last_np = max(last_np, mark_seed_group(g, stride, n, [&](int i) {
@@ -1163,7 +1177,8 @@ void engine_destroy(Engine* e) {
     for (DevBuf& b : e->gseeds) b.release();
     for (DevBuf& b : e->gqbits) b.release();
     for (DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->gdense,
-                      &e->heavy, &e->h_reads, &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds,
+                      &e->heavy, &e->hseeds, &e->hprobed, &e->h_reads, &e->h_offsets, &e->h_out,
+                      &e->h_dmax, &e->p_seeds,
                       &e->p_hits,
                       &e->p_hitoff, &e->p_partial, &e->p_table, &e->p_events, &e->p_hitlist,
                       &e->p_items, &e->p_misc, &e->p_dense})
@@ -1185,7 +1200,7 @@ size_t engine_bytes(const Engine* e) {
     for (const DevBuf& b : e->gseeds) s += b.bytes;
     for (const DevBuf& b : e->gqbits) s += b.bytes;
     for (const DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->gdense,
-                            &e->heavy,
+                            &e->heavy, &e->hseeds, &e->hprobed,
                             &e->h_reads, &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds,
                             &e->p_hits, &e->p_hitoff, &e->p_partial, &e->p_table, &e->p_events,
                             &e->p_hitlist, &e->p_items, &e->p_misc, &e->p_dense})
@@ -1201,7 +1216,8 @@ void engine_release(Engine* e) {
         e->gexec = nullptr;
     }
     e->gtab_ready = false;
-    for (DevBuf* b : {&e->packed, &e->gtab, &e->ghits, &e->gdense, &e->heavy, &e->h_reads,
+    for (DevBuf* b : {&e->packed, &e->gtab, &e->ghits, &e->gdense, &e->heavy, &e->hseeds,
+                      &e->hprobed, &e->h_reads,
                       &e->h_offsets,
                       &e->h_out, &e->h_dmax, &e->p_seeds, &e->p_hits, &e->p_hitoff, &e->p_partial,
                       &e->p_table, &e->p_events, &e->p_hitlist, &e->p_items, &e->p_misc, &e->p_dense})
@@ -1552,11 +1568,20 @@ static int plan_batch(const snap_index* idx, Engine* e, const uint64_t* d_offset
         plan->cl.off[q] = off;
         off += bp.st.cls_n[q];
     }
-    if (plan->light && (rc = light_prepare())) return rc;
+    if (plan->light) {
+        if ((rc = light_prepare())) return rc;
+        if ((rc = e->hseeds.ensure(n * kLightBucketMaxSeeds * sizeof(SeedRec), "handed-over probes")))
+            return rc;
+        if ((rc = e->hprobed.ensure(n, "handed-over flags"))) return rc;
+    }
     for (int q = 0; q < kClasses; ++q)
         if (bp.st.cls_n[q] > 0 &&
             (rc = plan_class(idx, e, d_offsets, n, p, d_out, bp, shape, q, stream, plan)))
             return rc;
+    for (int q = 0; q < kClasses; ++q) {
+        plan->a[q].hseeds = plan->light ? static_cast<const SeedRec*>(e->hseeds.p) : nullptr;
+        plan->a[q].hprobed = plan->light ? static_cast<const uint8_t*>(e->hprobed.p) : nullptr;
+    }
     // global candidate tables: one buffer for the largest class need (the class
     // launches run one after another and leave the tables empty)
     uint64_t slots = 0;
@@ -1594,8 +1619,11 @@ static int enqueue_batch(const snap_index* idx, Engine* e, const uint64_t* d_off
               "queue clear");
     if (plan.light) {
         // short reads: one thread each; the leftovers go to the warp kernel
+        SNAP_CUDA(cudaMemsetAsync(e->hprobed.p, 0, n, stream), "hand-over clear");
         if ((rc = launch_light(idx, e, d_offsets, n, p, d_out, stream, bp, plan.heavy_ids,
-                               plan.head + 4, plan.shape.light_threads)))
+                               plan.head + 4, plan.shape.light_threads,
+                               static_cast<SeedRec*>(e->hseeds.p),
+                               static_cast<uint8_t*>(e->hprobed.p))))
             return rc;
     }
     e->launches++;

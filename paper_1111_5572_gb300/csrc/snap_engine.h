@@ -34,6 +34,8 @@ struct Engine {
     DevBuf stats, head, packed, gtab, ghits, gdense, heavy;
     DevBuf gseeds[4];  // per-class per-warp seed records of long reads
     DevBuf gqbits[4];  // per-class per-warp q-gram bitmaps (large limits)
+    DevBuf hseeds;     // probe records of the reads the short-read bucket hands over
+    DevBuf hprobed;    // per read: 1 when hseeds holds its records
     bool gtab_ready = false;  // gtab holds only empty slots
     DevBuf h_reads, h_offsets, h_out, h_dmax;  // device copies for the host-buffer entry points
     PinnedBuf pin;
@@ -82,7 +84,7 @@ int light_prepare();
 int launch_light(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
                  const snap_params* p, snap_result* d_out, cudaStream_t stream,
                  const BatchPrep& bp, uint32_t* heavy_ids, unsigned long long* heavy_count,
-                 int threads);
+                 int threads, SeedRec* hseeds, uint8_t* hprobed);
 
 int prepare_batch(const snap_index* idx, Engine* e, const uint8_t* d_reads,
                   const uint64_t* d_offsets, uint64_t n, const snap_params* p,

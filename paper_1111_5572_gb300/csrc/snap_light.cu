@@ -61,6 +61,8 @@ struct LightArgs {
     snap_result* out;
     uint32_t* heavy_ids;
     unsigned long long* heavy_count;
+    SeedRec* hseeds;   // probe records of handed-over reads (kLightMaxSeeds per read)
+    uint8_t* hprobed;  // per read: 1 when hseeds holds them
     int* status;
     DevCounters* ctr;
 };
@@ -303,10 +305,16 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                     res_d = d_best;
                 }
             }
+            if (heavy && a.hseeds) {  // handed over after probing: the warp kernel
+                for (int i = 0; i < n; ++i)  // starts from these records
+                    a.hseeds[r * kLightMaxSeeds + i] = seeds[i];
+                a.hprobed[r] = 1;
+            }
         }
         if (heavy) {
             const unsigned long long at = atomicAdd(a.heavy_count, 1ull);
             a.heavy_ids[at] = (uint32_t)r;
+
         } else {
             unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.out + r);
             dst[0] = (unsigned long long)res_loc;
@@ -343,7 +351,7 @@ int light_prepare() {
 int launch_light(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,
                  const snap_params* p, snap_result* d_out, cudaStream_t stream,
                  const BatchPrep& bp, uint32_t* heavy_ids, unsigned long long* heavy_count,
-                 int threads) {
+                 int threads, SeedRec* hseeds, uint8_t* hprobed) {
     LightArgs a;
     memset(&a, 0, sizeof(a));
     a.genome = idx->genome_words;
@@ -367,6 +375,8 @@ int launch_light(const snap_index* idx, Engine* e, const uint64_t* d_offsets, ui
     a.out = d_out;
     a.heavy_ids = heavy_ids;
     a.heavy_count = heavy_count;
+    a.hseeds = hseeds;
+    a.hprobed = hprobed;
     BatchStats* d_st = static_cast<BatchStats*>(e->stats.p);
     a.status = &d_st->status;
     a.ctr = &d_st->ctr;
