@@ -142,8 +142,10 @@ int snap_index_free(snap_index* index);
 int snap_index_info_get(const snap_index* index, snap_index_info* out);
 
 /*
- * Align n_reads reads with Algorithm 1 (batched form: one persistent kernel per
- * length bucket, replayed from a cached CUDA graph).  Host buffers:
+ * Align n_reads reads with Algorithm 1 (batched form: a thread-per-read kernel
+ * for short reads, then one persistent kernel per read-length class with a warp
+ * or, for classes of few long reads, a block per read, the launch sequence
+ * replayed from a cached CUDA graph).  Host buffers:
  *   reads_ascii   the reads back to back; read r is
  *                 reads_ascii[read_offsets[r] .. read_offsets[r+1]).
  *   read_offsets  n_reads + 1 non-decreasing entries.
