@@ -64,3 +64,36 @@ def test_missing_library_raises(tmp_path):
             snap.load_library(str(tmp_path / "nope.so"))
         finally:
             snap._lib = None
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the binding's ctypes structures against the C compiler's layout of include/snap.h:
+    # every field at the same offset, every struct the same size
+    structs = {"snap_params": snap.snap_params, "snap_result": None,
+               "snap_index_info": snap.snap_index_info, "snap_call_stats": snap.snap_call_stats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "snap.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        fields = ([f for f in snap.RESULT_DTYPE.names if f != "pad"] if cls is None
+                  else [f for f, _ in cls._fields_])
+        for field in fields:
+            lines.append(f'printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = dict(line.rsplit(" ", 1) for line in
+               subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+               .stdout.splitlines())
+    for name, cls in structs.items():
+        if cls is None:
+            assert int(out[f"{name} size"]) == snap.RESULT_DTYPE.itemsize
+            for field in snap.RESULT_DTYPE.names:
+                if field != "pad":
+                    assert int(out[f"{name}.{field}"]) == snap.RESULT_DTYPE.fields[field][1]
+            continue
+        assert int(out[f"{name} size"]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(out[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
