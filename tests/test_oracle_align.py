@@ -356,3 +356,41 @@ def test_strided_index_workloads_stride_one_and_replay():
                 x = _rc(x)
             p = int(lit["location"][i])
             assert oracle.ed_dp(x, bytes(g[p:p + len(x) + 20])) == lit["edit_distance"][i]
+
+
+def test_against_exhaustive_search_on_a_tiny_genome():
+    # "Exhaustive SNAP": the bounded distance of every read at every genome position on
+    # both strands.  Exact check: a reported hit's distance is the exhaustive table's at
+    # its (p, strand).  Soft check (SNAP is a heuristic and only scores what its seeds
+    # vote for): at least 90% of the confident hits reach the exhaustive optimum.
+    rng = np.random.default_rng(31)
+    g = _rand(5000, 31)
+    for src, dst in ((200, 3000), (1200, 4200)):  # near repeats at 2% divergence
+        unit = bytearray(g[src:src + 300])
+        for i in rng.choice(300, 6, replace=False):
+            unit[i] = b"ACGT"[(b"ACGT".index(unit[i]) + 1) % 4]
+        g[dst:dst + 300] = unit
+    g = bytes(g)
+    reads = []
+    for k in range(60):
+        p = int(rng.integers(0, 5000 - 80))
+        r = bytearray(g[p:p + 60])
+        for i in rng.choice(60, int(rng.integers(0, 3)), replace=False):
+            r[i] = b"ACGT"[(b"ACGT".index(r[i]) + 1) % 4]
+        reads.append(bytes(r) if k % 2 == 0 else _rc(bytes(r)))
+    d_max, c = 8, 2
+    res, _ = _align(g, reads, max_dist=d_max, conf_diff=c)
+    L = d_max + c - 1
+    agree = confident = 0
+    for r, x in zip(res, reads):
+        X = [x, _rc(x)]
+        xs = [X[st] for st in (0, 1) for p in range(len(g))]
+        ts = [g[p:p + len(x) + L] for st in (0, 1) for p in range(len(g))]
+        lv, _ = oracle.ed_pairs(xs, ts, [L] * len(xs), with_dp=False)
+        d = np.where(lv < 0, 10_000, lv).reshape(2, len(g))
+        if r["location"] >= 0:
+            assert d[int(r["strand"]), int(r["location"])] == r["edit_distance"]
+        if r["cls"] == SINGLE:
+            confident += 1
+            agree += int(r["edit_distance"] == d.min())
+    assert confident >= 40 and agree / confident >= 0.9
