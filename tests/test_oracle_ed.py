@@ -11,7 +11,9 @@ than themselves:
   between strings), exhaustive over a binary alphabet;
 * hand-worked values;
 * the band theorem: ed_lv(L) == (ed_dp if ed_dp <= L else over), exhaustive over
-  ACGT for short strings and random long pairs at 0-30% error with limits up to 800.
+  ACGT for short strings and random long pairs at 0-30% error with limits up to 800;
+* Myers' bit-vector method (anchored start, free end), written here independently:
+  exhaustive over short ACGT strings and random pairs up to 1.2 kb.
 """
 import itertools
 import random
@@ -175,3 +177,57 @@ def test_band_theorem_text_cut():
                 assert d_cut == d_full
             else:
                 assert d_cut > L
+
+
+def _bitparallel_prefix_distance(x: str, t: str) -> int:
+    """min over j of Lev(x, t[0..j)) by the bit-vector method of Myers (1999) in
+    Hyyro's formulation: one machine word (here a Python int) per text column holds
+    the vertical differences of the column; the top row's horizontal difference is
+    +1 per column because the start is anchored (D[0][j] = j).  Written independently
+    of the oracle as a second way to the same integer."""
+    m = len(x)
+    if m == 0:
+        return 0
+    mask, high = (1 << m) - 1, 1 << (m - 1)
+    peq = {c: sum(1 << i for i, xc in enumerate(x) if xc == c) for c in "ACGT"}
+    pv, mv, score = mask, 0, m
+    best = score
+    for c in t:
+        eq = peq.get(c, 0)
+        xv = eq | mv
+        xh = ((((eq & pv) + pv) & mask) ^ pv) | eq
+        ph = (mv | ~(xh | pv)) & mask
+        mh = pv & xh
+        if ph & high:
+            score += 1
+        elif mh & high:
+            score -= 1
+        ph = ((ph << 1) | 1) & mask
+        mh = (mh << 1) & mask
+        pv = (mh | ~(xv | ph)) & mask
+        mv = ph & xv
+        best = min(best, score)
+    return best
+
+
+def test_table_equals_bit_parallel_exhaustive():
+    # every pair over ACGT with |x| <= 3 and |t| <= 5, and |x| = 4 with |t| <= 4
+    for lx in range(0, 5):
+        for x in ("".join(p) for p in itertools.product("ACGT", repeat=lx)):
+            for lt in range(0, 6 if lx <= 3 else 5):
+                for t in ("".join(p) for p in itertools.product("ACGT", repeat=lt)):
+                    assert oracle.ed_dp(x, t) == _bitparallel_prefix_distance(x, t), (x, t)
+
+
+@pytest.mark.parametrize("m,rate", [(60, 0.05), (150, 0.1), (400, 0.2), (1200, 0.05)])
+def test_table_and_reach_equal_bit_parallel_random(m, rate):
+    rng = random.Random(7 * m + int(rate * 100))
+    for _ in range(40):
+        x = "".join(rng.choice("ACGT") for _ in range(m))
+        t = _mutate(rng, x, rate) + "".join(rng.choice("ACGT") for _ in range(30))
+        if rng.random() < 0.3:  # an unrelated window
+            t = "".join(rng.choice("ACGT") for _ in range(len(t)))
+        d = _bitparallel_prefix_distance(x, t)
+        assert oracle.ed_dp(x, t) == d
+        L = rng.randint(0, m // 3)
+        assert oracle.ed_lv(x, t, L) == (d if d <= L else -1)
