@@ -4,11 +4,14 @@ Index ("Hash Index" subsection): every overlapping s-mer of the genome is indexe
 (window slid one base at a time).  Pinned against a brute-force scan of every genome
 position written with numpy, including palindromic seeds and the last window.
 
-Seed order (item 3 of the list after Algorithm 1): pinned against the offsets worked
-by hand from the paper's wording (tests/golden/seed_order_m100_s20.txt) and against
-invariants that hold for any (m, s): every offset in [0, m-s] used exactly once, the
-first floor(m/s) offsets are the non-overlapping ones, and each later shift pass is
-spread out as far as possible from the passes before it.
+Seed order (item 3 of the list after Algorithm 1): pinned against every offset of
+three shapes worked by hand from the paper's wording (tests/golden/seed_order_*.txt:
+m = 100 / s = 20, m = 64 / s = 16, m = 50 / s = 12) and against invariants that hold
+for any (m, s): every offset in [0, m-s] used exactly once, the first floor(m/s)
+offsets are the non-overlapping ones, and the passes spread out level by level: once
+the shifts of the halving levels up to k (s/2, then s/4 and 3s/4, ...) are all used,
+they are 2^k points that cut [0, s) into gaps of floor(s/2^k) or ceil(s/2^k) bases,
+the most even spacing integers allow.
 """
 import os
 
@@ -34,11 +37,39 @@ def _revcomp(a: bytes) -> bytes:
     return a[::-1].translate(bytes.maketrans(b"ACGT", b"TGCA"))
 
 
-def test_seed_order_matches_paper_example():
-    expect = _golden_ints("seed_order_m100_s20.txt")
-    offs, pass0 = oracle.seed_offsets(100, 20, len(expect))
+@pytest.mark.parametrize("m,s,name", [(100, 20, "seed_order_m100_s20.txt"),
+                                      (64, 16, "seed_order_m64_s16.txt"),
+                                      (50, 12, "seed_order_m50_s12.txt")])
+def test_seed_order_matches_hand_worked_offsets(m, s, name):
+    expect = _golden_ints(name)
+    assert len(expect) == m - s + 1  # the golden files list every window
+    offs, pass0 = oracle.seed_offsets(m, s, 10 ** 6)
     assert offs == expect
-    assert pass0 == [True] * 5 + [False] * (len(expect) - 5)
+    k = m // s
+    assert pass0 == [True] * k + [False] * (len(expect) - k)
+    # any prefix is the first n seeds
+    for n in (1, k, k + 1, 17, len(expect) - 1):
+        assert oracle.seed_offsets(m, s, n)[0] == expect[:n]
+
+
+def _pass_shifts(s):
+    """Shift of every pass, in order: the first offset of each pass of a read long
+    enough that every pass has one (a pass starts below s, later offsets do not)."""
+    offs, _ = oracle.seed_offsets(4 * s, s, 10 ** 6)
+    return [o for o in offs if o < s]
+
+
+@pytest.mark.parametrize("s", [8, 12, 16, 17, 20, 24, 31, 32])
+def test_seed_passes_spread_out_level_by_level(s):
+    shifts = _pass_shifts(s)
+    assert sorted(shifts) == list(range(s))  # every shift once
+    assert shifts[0] == 0 and shifts[1] == s // 2
+    k = 1
+    while (1 << k) <= s:
+        used = sorted(shifts[:1 << k]) + [s]
+        gaps = {b - a for a, b in zip(used, used[1:])}
+        assert gaps <= {s >> k, -(-s >> k)}, (k, used)
+        k += 1
 
 
 @pytest.mark.parametrize("m,s", [(100, 20), (125, 20), (37, 8), (1000, 20), (64, 32),
