@@ -73,6 +73,15 @@ def _args():
     ap.add_argument("--stride", type=int, default=1,
                     help="stride-k index: index windows at multiples of k, probe each seed "
                          "at k offsets (1 = every window, the default)")
+    ap.add_argument("--calls-per-step", type=int, default=0,
+                    help="align calls per timed step over the workload's reads (0 = enough "
+                         "for --min-timed-s of timed work, so the clock record has several "
+                         "samples); consecutive calls alternate between two device copies "
+                         "of the reads")
+    ap.add_argument("--min-timed-s", type=float, default=1.5)
+    ap.add_argument("--sweep-gather", action="store_true",
+                    help="the random-gather ceiling over chunk sizes, chunks in flight per "
+                         "thread and threads per SM (one JSON line)")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up plus the timed steps only (no plain form, e2e or CPU "
                          "baseline): the command to run under ncu")
@@ -81,6 +90,7 @@ def _args():
     if args.profile:
         args.no_plain = args.no_cpu_baseline = True
         args.e2e_steps = 0
+        args.calls_per_step = args.calls_per_step or 1
     return args
 
 
@@ -206,8 +216,8 @@ def _kernel_source_hash():
 
 
 def _ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per read from a committed ncu summary, if taken on these kernel
-    sources and this workload."""
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, if taken on
+    these kernel sources and this workload."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -219,6 +229,57 @@ def _ncu_traffic(kernel: str, workload: str):
     except Exception:
         pass
     return None
+
+
+GATHER_ILP = (4, 8, 16)
+GATHER_THREADS_PER_SM = (1024, 1536, 2048)
+
+
+def gather_ceiling(snap, chunks=(32, 64), ilps=GATHER_ILP, tps=GATHER_THREADS_PER_SM):
+    """The random-gather ceiling: the best GB/s of independent random reads of one
+    aligned chunk over a sweep of chunks in flight per thread and threads per SM
+    (8 GiB buffer, 2^28 reads per point)."""
+    out = {}
+    for cb in chunks:
+        pts = [{"ilp": i, "threads_per_sm": t,
+                "gbs": snap.measure_gather_config(8 << 30, cb, 1 << 28, i, t)}
+               for i in ilps for t in tps]
+        best = max(pts, key=lambda q: q["gbs"])
+        out[f"chunk{cb}_gbs"] = best["gbs"]
+        out[f"chunk{cb}_best_shape"] = {"ilp": best["ilp"],
+                                        "threads_per_sm": best["threads_per_sm"]}
+        out[f"chunk{cb}_sweep_min_gbs"] = min(q["gbs"] for q in pts)
+    out["sweep"] = {"ilp": list(ilps), "threads_per_sm": list(tps)}
+    return out
+
+
+def run_gather_sweep(args):
+    """--sweep-gather: the random-gather ceiling over chunk sizes 16-128 bytes,
+    1-16 chunks in flight per thread and 256-2048 threads per SM; one JSON line."""
+    import torch
+
+    import paper_1111_5572_gb300 as snap
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    points = []
+    with ClockSampler(0) as clk:
+        for cb in (16, 32, 64, 128):
+            for i in (1, 2, 4, 8, 16):
+                for t in (256, 512, 1024, 1536, 2048):
+                    g = snap.measure_gather_config(8 << 30, cb, 1 << 28, i, t)
+                    points.append({"chunk_bytes": cb, "ilp": i, "threads_per_sm": t,
+                                   "gbs": g, "g_reads_per_s": g / cb})
+    best = {cb: max((q for q in points if q["chunk_bytes"] == cb), key=lambda q: q["gbs"])
+            for cb in (16, 32, 64, 128)}
+    peak, peak_kind = _peaks()
+    line = {"mode": "sweep_gather", "unit": "GB/s", "buffer_bytes": 8 << 30,
+            "reads_per_point": 1 << 28, "peak_copy_gbs": peak, "peak_kind": peak_kind,
+            "best": {str(cb): q for cb, q in best.items()}, "points": points,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def make_workload(args, rank: int):
@@ -346,6 +407,10 @@ def run_ours(args):
     d_o = torch.from_numpy(rd.offsets.view(np.int64)).to(dev)
     d_out = torch.zeros((n, 16), dtype=torch.uint8, device=dev)
     d_dpr = None if dpr is None else torch.from_numpy(dpr).to(dev)
+    # a second device copy of the reads and results: consecutive calls of a step
+    # alternate between the two, so a call never finds the previous call's reads
+    # in L2 (the index itself is far larger than L2)
+    copies = [(d_b, d_out), (d_b.clone(), torch.zeros_like(d_out))]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     # a stream of its own (not the legacy default stream) so the batched form can
     # replay its launch sequence as a CUDA graph
@@ -353,85 +418,133 @@ def run_ours(args):
 
     batch = max(1, min(args.batch, n))
 
-    def one_step(form_plain):
+    def one_pass(form_plain, which=0):
         # all the workload's reads, `batch` reads per call; returns each call's stats
+        db, dout = copies[which]
         calls = []
         for b0 in range(0, n, batch):
             nb = min(batch, n - b0)
-            idx.align_device(d_b, d_o[b0:b0 + nb + 1], d_out[b0:b0 + nb],
+            idx.align_device(db, d_o[b0:b0 + nb + 1], dout[b0:b0 + nb],
                              d_max_dist_per_read=None if d_dpr is None else d_dpr[b0:b0 + nb],
                              stream=stream, plain=form_plain, **params)
             calls.append(idx.last_call_stats())
         return calls
 
-    def timed(form_plain, steps, warmup):
-        for _ in range(warmup):
+    def flush_l2():
+        with torch.cuda.stream(stream):  # ordered before the step's first event
             flush.zero_()
-            one_step(form_plain)
+
+    def pass_ms(form_plain, reps=3):
+        # device time of one pass over the workload (to size the timed steps)
+        best = 1e30
+        for k in range(reps):
+            flush_l2()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_pass(form_plain, k & 1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    def timed(form_plain, steps, warmup, passes):
+        for k in range(warmup):
+            flush_l2()
+            one_pass(form_plain, k & 1)
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(steps)]
-        stats = []
+        calls = []
         wall0 = time.perf_counter()
         with ClockSampler(local) as clk:
             for k in range(steps):
-                flush.zero_()  # L2 flush outside the event pair
+                flush_l2()  # L2 flush on the timed stream, before the step's first event
                 evs[k][0].record(stream)
-                calls = one_step(form_plain)
+                step_calls = []
+                for q in range(passes):
+                    step_calls += one_pass(form_plain, q & 1)
                 evs[k][1].record(stream)
-                agg = dict(calls[-1])
-                for key in ("kernel_launches", "align_ms", "reads", "read_bases", "seeds",
-                            "slot_reads", "list_entries", "ed_calls", "ed_over",
-                            "window_bytes", "ed_filtered", "probe_ms", "distance_ms"):
-                    agg[key] = sum(c[key] for c in calls)
-                stats.append(agg)
+                calls = step_calls
             torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         step_ms = [a.elapsed_time(b) for a, b in evs]
-        return step_ms, stats, clk.summary(), wall
+        return step_ms, calls, clk.summary(), wall
 
-    step_ms, stats, clocks, wall = timed(plain, args.steps, args.warmup)
-    value, total_s = job_throughput(sum(step_ms) / 1e3, n, args.steps, ws, dev)
+    for k in range(args.warmup):  # warm-up (tuning, graphs) before sizing the steps
+        one_pass(plain, k & 1)
+    passes = args.calls_per_step
+    if passes <= 0:
+        t_pass = pass_ms(plain) / 1e3
+        passes = int(max(1, min(1000, np.ceil(args.min_timed_s / (args.steps * t_pass)))))
+    step_ms, calls, clocks, wall = timed(plain, args.steps, args.warmup, passes)
+    reads_per_step = n * passes
+    value, total_s = job_throughput(sum(step_ms) / 1e3, reads_per_step, args.steps, ws, dev)
     ms_per_step = total_s * 1e3 / args.steps
-    launches = int(sum(s["kernel_launches"] for s in stats))
+    # every kernel launch of the last step's calls (stats, pack and align kernels)
+    launches = int(sum(c["kernel_launches"] for c in calls)) * args.steps
     got = d_out.cpu().numpy().view(snap.RESULT_DTYPE).reshape(-1)
 
-    # roofline of the main align kernel(s): algorithmic bytes from the kernels' own counters
-    st = stats[-1]
-    align_ms = float(np.mean([s["align_ms"] for s in stats]))
-    alg_bytes = (st["read_bases"] / 4 + 8 * st["reads"] + 16 * st["reads"] +
-                 16 * st["slot_reads"] + 4 * st["list_entries"] + st["window_bytes"])
+    # Roofline of the dominant kernel: algorithmic bytes per the survey's per-unit
+    # figures (read in 100 B of bases at m = 100, i.e. m bytes, + 16 B result per read
+    # finished; 32 B per probe; 4 B per out-of-line list entry; 64 B per scored
+    # candidate) over the kernel's event-timed duration on the launch stream.
+    mean_m = float(rd.lengths().mean())
     peak, peak_kind = _peaks()
-    achieved = alg_bytes / (align_ms / 1e3) / 1e9
-    kname = "plain_stages" if plain else "align_span"
-    tr = _ncu_traffic(kname, w.name)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
+    nc = len(calls)
+    mean = lambda key: float(np.mean([c[key] for c in calls]))
+    first = calls[0]  # counters of one call (every call aligns the same reads)
+    pc = [c for c in calls[:max(1, len(calls) // passes)]]  # the calls of one pass
+    tot = lambda key: float(sum(c[key] for c in pc))
+
+    def alg_bytes(reads, probes, lists, eds):
+        return reads * (mean_m + 16) + 32 * probes + 4 * lists + 64 * eds
+
+    span_bytes = alg_bytes(tot("reads"), tot("seeds"), tot("list_entries"), tot("ed_calls"))
+    span_ms = float(sum(c["align_ms"] for c in calls)) / passes
+    light_ms = float(sum(c["light_ms"] for c in calls)) / passes
+    light_bytes = alg_bytes(tot("reads_light"), tot("light_seeds"), tot("light_list_entries"),
+                            tot("light_ed_calls"))
+    if not plain and light_ms > 0.5 * span_ms:
+        kname, kbytes, kms = "k_align_light", light_bytes, light_ms
+    elif not plain:
+        kname = "k_align_fused/k_align_team (per length class)"
+        kbytes, kms = span_bytes - light_bytes, span_ms - light_ms
+    else:
+        kname, kbytes, kms = "plain stages", span_bytes, span_ms
+    achieved = kbytes / (kms / 1e3) / 1e9
+    tr = _ncu_traffic(kname.split(" ")[0].split("/")[0], w.name)
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                 "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                "traffic": None if tr is None else tr["dram_bytes_per_read"] * st["reads"],
-                "kernel": ("k_plain_probe + k_plain_candidates + k_plain_distance + "
-                           "k_plain_replay" if plain else
-                           "k_align_light + k_split_classes + k_align_fused/k_align_team "
-                           "per length class"),
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "kernel_ms": align_ms,
-                "counters": {k: st[k] for k in ("seeds", "slot_reads", "list_entries",
-                                                "ed_calls", "ed_over", "window_bytes",
-                                                "ed_filtered")}}
+                # DRAM bytes of one launch from a committed ncu capture of this kernel's
+                # current source on this workload (scaled to the call's read count)
+                "traffic": None if tr is None else
+                tr["dram_bytes_per_launch"] * tot("reads") / tr["reads"],
+                "algorithmic_bytes_per_launch": kbytes, "kernel_ms": kms,
+                "bytes_per_unit": {"read": f"{mean_m:.0f} + 16", "probe": 32, "list_entry": 4,
+                                   "scored_candidate": 64},
+                "align_span": {"kernels": "k_align_light + k_split_classes + "
+                                          "k_align_fused/k_align_team per length class",
+                               "algorithmic_bytes": span_bytes, "ms": span_ms,
+                               "achieved": span_bytes / (span_ms / 1e3) / 1e9,
+                               "frac": span_bytes / (span_ms / 1e3) / 1e9 / peak},
+                "counters": {k: tot(k) for k in ("reads", "seeds", "slot_reads", "list_entries",
+                                                 "ed_calls", "ed_over", "window_bytes",
+                                                 "ed_filtered", "reads_light", "light_seeds",
+                                                 "light_list_entries", "light_ed_calls")}}
     # the practical ceiling of this traffic: independent random reads of one
     # aligned chunk (a 64-byte index bucket, a 32-byte sector); not under
     # --profile, whose launch list should hold the aligner's kernels only
     roofline["gather_ceiling"] = None
     if not args.profile:
         try:
-            gc = {f"chunk{cb}_gbs": snap.measure_gather(8 << 30, cb, 1 << 28)
-                  for cb in (32, 64)}
+            gc = gather_ceiling(snap)
             gc["frac_of_chunk64"] = achieved / gc["chunk64_gbs"]
             roofline["gather_ceiling"] = gc
         except Exception as e:  # a measurement aid, not the product
@@ -442,37 +555,43 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": w.name, "genome_bp": w.G, "repeat_frac": w.repeat_frac,
-                   "reads_per_step": n, "reads_per_call": batch,
+                   "reads_per_step": reads_per_step, "reads_per_call": batch,
+                   "passes_per_step": passes,
                    "read_len": "100" if w.len_mode == 0 else "mixed",
                    "seed_len": w.seed_len, "index_stride": args.stride, **params,
                    "form": args.form,
-                   "l2": "flushed between steps (512 MiB write)",
+                   "l2": "flushed before every step (512 MiB write on the timed stream); "
+                         "within a step, consecutive passes alternate between two device "
+                         "copies of the reads",
                    "parallelism": "replicas" if ws > 1 else "single"},
-        "bases_per_s": value * float(rd.lengths().mean()),
+        "ms_per_pass": ms_per_step / passes,
+        "bases_per_s": value * mean_m,
         "index_build_s": build_s, "index_device_gb": info["device_bytes"] / 1e9,
         "input_gen_s": gen_s, "wall_s_timed": wall,
         "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
-        "launch_shape": {k: st[k] for k in ("light_threads", "warps_per_block", "table_slots",
-                                            "graph_replay", "team_classes")},
+        "stage_ms_per_call": {k: mean(k) for k in ("stats_ms", "pack_ms", "align_ms",
+                                                   "light_ms", "total_ms", "host_plan_ms")},
+        "launch_shape": {k: first[k] for k in ("light_threads", "warps_per_block",
+                                               "table_slots", "graph_replay", "team_classes")},
     }
 
     # the plain one-launch-per-stage form on the same GPU and inputs
     if not plain and not args.no_plain:
         try:
-            p_ms, p_stats, _, _ = timed(True, max(3, args.steps // 4), 3)
+            p_ms, p_calls, _, _ = timed(True, max(3, args.steps // 4), 3, passes)
             p_got = d_out.cpu().numpy().view(snap.RESULT_DTYPE).reshape(-1)
             same = all(np.array_equal(p_got[f], got[f]) for f in
                        ("location", "edit_distance", "strand", "cls"))
             p_total = sum(p_ms) / 1e3
-            line["plain"] = {"value": n * len(p_ms) / p_total, "unit": "reads/s",
-                             "ms_per_step": p_total * 1e3 / len(p_ms),
-                             "gpu_launches_per_step": int(p_stats[-1]["kernel_launches"]),
+            line["plain"] = {"value": reads_per_step * len(p_ms) / p_total, "unit": "reads/s",
+                             "ms_per_pass": p_total * 1e3 / len(p_ms) / passes,
+                             "gpu_launches_per_call": int(p_calls[-1]["kernel_launches"]),
                              "identical_results": bool(same)}
             # the probe path alone: the plain form's seed-probe stage kernel, whose
             # traffic is the packed s-mer (8 B) and seed record (16 B) per seed, the
             # 16-byte index slots it reads, and per read its offsets and hit count
-            ps = p_stats[-1]
-            probe_ms = float(np.mean([q["probe_ms"] for q in p_stats]))
+            ps = p_calls[-1]
+            probe_ms = float(np.mean([q["probe_ms"] for q in p_calls]))
             probe_bytes = 24 * ps["seeds"] + 16 * ps["slot_reads"] + 20 * ps["reads"]
             if probe_ms > 0:
                 gbs = probe_bytes / (probe_ms / 1e3) / 1e9
@@ -482,7 +601,7 @@ def run_ours(args):
                     "frac_of_nominal": gbs / NOMINAL_HBM_GBS,
                     "probes": ps["seeds"], "slot_reads": ps["slot_reads"],
                     "probes_per_s": ps["seeds"] / (probe_ms / 1e3)}
-                gc = roofline.get("gather_ceiling", {})
+                gc = roofline.get("gather_ceiling") or {}
                 if "chunk64_gbs" in gc:
                     line["probe_stage"]["frac_of_gather_chunk64"] = gbs / gc["chunk64_gbs"]
             line["batched_over_plain"] = line["value"] / line["plain"]["value"]
@@ -698,6 +817,8 @@ def main():
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.sweep_gather:
+        return run_gather_sweep(args)
     if args.sweep_hmax:
         return run_sweep(args, "max_hits", [int(x) for x in args.sweep_hmax.split(",") if x])
     if args.sweep_first_seeds:

@@ -265,6 +265,20 @@ typedef struct {
                                  traffic is seeds x (8 + 16) bytes + 16 per slot read);
                                  0 for the batched form, where probes are fused */
     double distance_ms;       /* plain form: the edit-distance stage kernel alone */
+    double host_plan_ms;      /* host time from the batch statistics reaching the host to
+                                 the last align launch being enqueued (planning, graph
+                                 update); the device idles for whatever part of it
+                                 outlasts the read-packing kernel */
+    /* batched form: the thread-per-read kernel alone (its share of the counters above,
+       and its device time: the device clock from its first block's start to its last
+       block's end) */
+    double light_ms;
+    uint64_t reads_light;         /* reads it finished (the rest went to the warp kernels) */
+    uint64_t light_seeds;
+    uint64_t light_slot_reads;
+    uint64_t light_list_entries;
+    uint64_t light_ed_calls;
+    uint64_t light_window_bytes;
 } snap_call_stats;
 
 int snap_last_call_stats(const snap_index* index, snap_call_stats* out);
@@ -305,6 +319,14 @@ int snap_index_configure(snap_index* index, int autotune, int cuda_graphs, int t
  * not fit, SNAP_E_INVAL for other sizes. */
 int snap_measure_gather(uint64_t buffer_bytes, uint32_t chunk_bytes, uint64_t n_reads,
                         double* gbs_out);
+
+/* The same measurement with its launch shape as arguments, to find the ceiling
+ * rather than one point under it: chunk_bytes 16, 32, 64 or 128; ilp = chunks in
+ * flight per thread (1, 2, 4, 8 or 16); threads_per_sm a multiple of 256 in
+ * [256, 2048].  snap_measure_gather is ilp 4 at 2048 threads per SM.  Errors as
+ * snap_measure_gather (SNAP_E_INVAL for other shapes). */
+int snap_measure_gather_config(uint64_t buffer_bytes, uint32_t chunk_bytes, uint64_t n_reads,
+                               int ilp, int threads_per_sm, double* gbs_out);
 
 /* Message for the last failed call on this thread ("" if none). */
 const char* snap_last_error(void);

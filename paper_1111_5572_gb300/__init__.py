@@ -28,7 +28,7 @@ EXPORTS = ("snap_index_build", "snap_index_build_stride", "snap_index_free", "sn
            "snap_align_device", "snap_align_plain_device", "snap_align_plain",
            "snap_server_create", "snap_server_submit", "snap_server_wait", "snap_server_destroy",
            "snap_last_call_stats", "snap_align_device_noalloc", "snap_index_configure",
-           "snap_measure_gather",
+           "snap_measure_gather", "snap_measure_gather_config",
            "snap_last_error")
 
 
@@ -62,7 +62,11 @@ class snap_call_stats(ctypes.Structure):
                 ("warps_per_block", ctypes.c_int32), ("table_slots", ctypes.c_int32),
                 ("graph_replay", ctypes.c_int32), ("team_classes", ctypes.c_int32),
                 ("ed_filtered", ctypes.c_uint64), ("probe_ms", ctypes.c_double),
-                ("distance_ms", ctypes.c_double)]
+                ("distance_ms", ctypes.c_double), ("host_plan_ms", ctypes.c_double),
+                ("light_ms", ctypes.c_double), ("reads_light", ctypes.c_uint64),
+                ("light_seeds", ctypes.c_uint64), ("light_slot_reads", ctypes.c_uint64),
+                ("light_list_entries", ctypes.c_uint64), ("light_ed_calls", ctypes.c_uint64),
+                ("light_window_bytes", ctypes.c_uint64)]
 
 
 _lib = None
@@ -95,6 +99,8 @@ def load_library(path: str = LIB_PATH):
     lib.snap_last_call_stats.argtypes = [vp, P(snap_call_stats)]
     lib.snap_index_configure.argtypes = [vp, i32, i32, i32]
     lib.snap_measure_gather.argtypes = [u64, ctypes.c_uint32, u64, P(ctypes.c_double)]
+    lib.snap_measure_gather_config.argtypes = [u64, ctypes.c_uint32, u64, i32, i32,
+                                               P(ctypes.c_double)]
     lib.snap_last_error.argtypes = []
     lib.snap_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -127,6 +133,17 @@ def measure_gather(buffer_bytes: int = 8 << 30, chunk_bytes: int = 32,
     out = ctypes.c_double()
     _check(load_library().snap_measure_gather(int(buffer_bytes), int(chunk_bytes), int(n_reads),
                                               ctypes.byref(out)), "snap_measure_gather")
+    return out.value
+
+
+def measure_gather_config(buffer_bytes: int = 8 << 30, chunk_bytes: int = 64,
+                          n_reads: int = 1 << 28, ilp: int = 4, threads_per_sm: int = 2048) -> float:
+    """snap_measure_gather_config: the same measurement at a given launch shape."""
+    out = ctypes.c_double()
+    _check(load_library().snap_measure_gather_config(int(buffer_bytes), int(chunk_bytes),
+                                                     int(n_reads), int(ilp), int(threads_per_sm),
+                                                     ctypes.byref(out)),
+           "snap_measure_gather_config")
     return out.value
 
 

@@ -40,25 +40,59 @@ constexpr unsigned long long kKeyMask = (1ull << 33) - 1;
 // ---------------------------------------------------------------------------
 // batch statistics and validation
 // ---------------------------------------------------------------------------
-__global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, int s, int stride,
-                             int num_seeds, int d_max, int c, int h_max,
-                             const int32_t* __restrict__ dmax_per_read, BatchStats* st) {
-    unsigned int my_len = 0;
-    int my_L0 = 0, my_n = 0, bad = 0;
-    unsigned long long my_hits = 0, my_light = 0;
-    unsigned long long c_n[kClasses] = {0, 0, 0, 0}, c_hits[kClasses] = {0, 0, 0, 0};
-    unsigned int c_len[kClasses] = {0, 0, 0, 0};
-    int c_L0[kClasses] = {0, 0, 0, 0}, c_seeds[kClasses] = {0, 0, 0, 0};
+// Partial statistics of one warp (reduced across the block in shared memory
+// before one set of atomics per block).
+struct StatsPart {
+    unsigned long long hits, light;
+    unsigned long long c_n[kClasses], c_hits[kClasses];
+    unsigned int len, c_len[kClasses];
+    int bad, L0, nseeds, c_L0[kClasses], c_seeds[kClasses];
+};
+
+__device__ __forceinline__ void stats_merge(StatsPart& a, const StatsPart& b) {
+    a.bad |= b.bad;
+    a.len = max(a.len, b.len);
+    a.L0 = max(a.L0, b.L0);
+    a.nseeds = max(a.nseeds, b.nseeds);
+    a.hits = b.hits > a.hits ? b.hits : a.hits;
+    a.light += b.light;
+#pragma unroll
+    for (int q = 0; q < kClasses; ++q) {
+        a.c_n[q] += b.c_n[q];
+        a.c_len[q] = max(a.c_len[q], b.c_len[q]);
+        a.c_L0[q] = max(a.c_L0[q], b.c_L0[q]);
+        a.c_seeds[q] = max(a.c_seeds[q], b.c_seeds[q]);
+        a.c_hits[q] = b.c_hits[q] > a.c_hits[q] ? b.c_hits[q] : a.c_hits[q];
+    }
+}
+
+constexpr int kStatsThreads = 256;
+
+// Grid of the statistics kernel: a few blocks per SM (each block merges its
+// threads' partials before its atomics, so fewer blocks mean fewer atomics on
+// the same few addresses).
+inline unsigned stats_grid(int sms, uint64_t n) {
+    uint64_t want = (n + kStatsThreads - 1) / kStatsThreads;
+    const uint64_t cap = (uint64_t)sms * 4;
+    return (unsigned)std::max<uint64_t>(1, std::min(want, cap));
+}
+
+__global__ void __launch_bounds__(kStatsThreads)
+k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, int s, int stride, int num_seeds,
+             int d_max, int c, int h_max, const int32_t* __restrict__ dmax_per_read,
+             BatchStats* st) {
+    StatsPart my;
+    memset(&my, 0, sizeof(my));
     for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
          r += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t a = offsets[r], b = offsets[r + 1];
         if (b < a) {
-            bad |= kStBadOffsets;
+            my.bad |= kStBadOffsets;
             continue;
         }
         const uint64_t m = b - a;
         if (m > (uint64_t)kMaxReadLen) {
-            bad |= kStReadTooLong;
+            my.bad |= kStReadTooLong;
             continue;
         }
         int nn = 0;
@@ -66,106 +100,143 @@ __global__ void k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, i
             nn = num_seeds > 0 ? num_seeds : (int)m / s;
             nn = min(nn, (int)m - s + 1);
         }
-        if (nn > kMaxSeeds) bad |= kStTooManySeeds;
+        if (nn > kMaxSeeds) my.bad |= kStTooManySeeds;
         nn *= stride;  // probe slots from here on (stride-k index)
         const int dm = dmax_per_read ? dmax_per_read[r] : d_max;
-        if (dm < 0) bad |= kStBadDmax;
-        my_len = max(my_len, (unsigned int)m);
-        my_L0 = max(my_L0, dm + c - 1);
-        my_light += (m <= (uint64_t)kLightBucketMaxM && nn <= kLightBucketMaxSeeds &&
+        if (dm < 0) my.bad |= kStBadDmax;
+        const unsigned long long hh = (unsigned long long)nn * (unsigned long long)h_max;
+        my.len = max(my.len, (unsigned int)m);
+        my.L0 = max(my.L0, dm + c - 1);
+        my.nseeds = max(my.nseeds, nn);
+        my.hits = hh > my.hits ? hh : my.hits;
+        my.light += (m <= (uint64_t)kLightBucketMaxM && nn <= kLightBucketMaxSeeds &&
                      dm + c - 1 <= kLightBucketMaxL);
         const int k = length_class(m);
 #pragma unroll
         for (int q = 0; q < kClasses; ++q) {
             if (q != k) continue;
-            c_n[q] += 1;
-            c_len[q] = max(c_len[q], (unsigned int)m);
-            c_L0[q] = max(c_L0[q], dm + c - 1);
-            c_seeds[q] = max(c_seeds[q], nn);
-            const unsigned long long hh = (unsigned long long)nn * (unsigned long long)h_max;
-            c_hits[q] = hh > c_hits[q] ? hh : c_hits[q];
+            my.c_n[q] += 1;
+            my.c_len[q] = max(my.c_len[q], (unsigned int)m);
+            my.c_L0[q] = max(my.c_L0[q], dm + c - 1);
+            my.c_seeds[q] = max(my.c_seeds[q], nn);
+            my.c_hits[q] = hh > my.c_hits[q] ? hh : my.c_hits[q];
         }
-        my_n = max(my_n, nn);
-        my_hits = max(my_hits, (unsigned long long)nn * (unsigned long long)h_max);
     }
-    // one atomic per warp and field (all threads of a warp reach this point)
+    // warp partials in shared memory, merged by thread 0, then one atomic per field
+    __shared__ StatsPart part[kStatsThreads / 32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        bad |= __shfl_xor_sync(kFull, bad, o);
-        my_len = max(my_len, __shfl_xor_sync(kFull, my_len, o));
-        my_L0 = max(my_L0, __shfl_xor_sync(kFull, my_L0, o));
-        my_n = max(my_n, __shfl_xor_sync(kFull, my_n, o));
-        const unsigned long long h = __shfl_xor_sync(kFull, my_hits, o);
-        my_hits = h > my_hits ? h : my_hits;
-        my_light += __shfl_xor_sync(kFull, my_light, o);
+        StatsPart other;
+        other.bad = __shfl_xor_sync(kFull, my.bad, o);
+        other.len = __shfl_xor_sync(kFull, my.len, o);
+        other.L0 = __shfl_xor_sync(kFull, my.L0, o);
+        other.nseeds = __shfl_xor_sync(kFull, my.nseeds, o);
+        other.hits = __shfl_xor_sync(kFull, my.hits, o);
+        other.light = __shfl_xor_sync(kFull, my.light, o);
 #pragma unroll
         for (int q = 0; q < kClasses; ++q) {
-            c_n[q] += __shfl_xor_sync(kFull, c_n[q], o);
-            c_len[q] = max(c_len[q], __shfl_xor_sync(kFull, c_len[q], o));
-            c_L0[q] = max(c_L0[q], __shfl_xor_sync(kFull, c_L0[q], o));
-            c_seeds[q] = max(c_seeds[q], __shfl_xor_sync(kFull, c_seeds[q], o));
-            const unsigned long long hh = __shfl_xor_sync(kFull, c_hits[q], o);
-            c_hits[q] = hh > c_hits[q] ? hh : c_hits[q];
+            other.c_n[q] = __shfl_xor_sync(kFull, my.c_n[q], o);
+            other.c_len[q] = __shfl_xor_sync(kFull, my.c_len[q], o);
+            other.c_L0[q] = __shfl_xor_sync(kFull, my.c_L0[q], o);
+            other.c_seeds[q] = __shfl_xor_sync(kFull, my.c_seeds[q], o);
+            other.c_hits[q] = __shfl_xor_sync(kFull, my.c_hits[q], o);
         }
+        stats_merge(my, other);
     }
-    if ((threadIdx.x & 31) == 0) {
-        if (bad) atomicOr(&st->status, bad);
-        atomicMax(&st->max_len, my_len);
-        atomicMax(&st->max_L0, my_L0);
-        atomicMax(&st->max_seeds, my_n);
-        atomicMax(&st->max_hits_bound, my_hits);
-        if (my_light) atomicAdd(&st->n_light, my_light);
+    if (lane == 0) part[wib] = my;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) stats_merge(my, part[w]);
+        if (my.bad) atomicOr(&st->status, my.bad);
+        atomicMax(&st->max_len, my.len);
+        atomicMax(&st->max_L0, my.L0);
+        atomicMax(&st->max_seeds, my.nseeds);
+        atomicMax(&st->max_hits_bound, my.hits);
+        if (my.light) atomicAdd(&st->n_light, my.light);
 #pragma unroll
         for (int q = 0; q < kClasses; ++q) {
-            if (!c_n[q]) continue;
-            atomicAdd(&st->cls_n[q], c_n[q]);
-            atomicMax(&st->cls_max_len[q], c_len[q]);
-            atomicMax(&st->cls_max_L0[q], c_L0[q]);
-            atomicMax(&st->cls_max_seeds[q], c_seeds[q]);
-            atomicMax(&st->cls_max_hits[q], c_hits[q]);
+            if (!my.c_n[q]) continue;
+            atomicAdd(&st->cls_n[q], my.c_n[q]);
+            atomicMax(&st->cls_max_len[q], my.c_len[q]);
+            atomicMax(&st->cls_max_L0[q], my.c_L0[q]);
+            atomicMax(&st->cls_max_seeds[q], my.c_seeds[q]);
+            atomicMax(&st->cls_max_hits[q], my.c_hits[q]);
+        }
+        if (blockIdx.x == 0) {
+            st->total_bases = offsets[n] - offsets[0];
+            if (offsets[n] < offsets[0]) atomicOr(&st->status, kStBadOffsets);
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->total_bases = offsets[n] - offsets[0];
-        if (offsets[n] < offsets[0]) atomicOr(&st->status, kStBadOffsets);
+}
+
+// 16 ASCII bases (four little-endian 32-bit words) to one word of 2-bit codes;
+// sets *bad when a byte is not one of A, C, G, T.  Four bases per operation:
+// code = ((c >> 1) ^ (c >> 2)) & 3 on every byte at once (the shifted-in bits
+// land above bit 1 of each byte and are masked off), the four 2-bit codes are
+// gathered into one byte, and each byte is checked by rebuilding the letter of
+// its code with a byte permutation of "ACGT" and comparing.
+__device__ __forceinline__ uint32_t pack16_ascii(const uint32_t (&parts)[4], bool* bad) {
+    uint32_t word = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t v = parts[q];
+        const uint32_t t = ((v >> 1) ^ (v >> 2)) & 0x03030303u;  // code k at bits 8k, 8k+1
+        const uint32_t u = t | (t >> 6);                          // codes 0,1 at bits 0-3; 2,3 at 16-19
+        word |= ((u & 0xfu) | ((u >> 12) & 0xf0u)) << (8 * q);
+        const uint32_t sel = (t & 3u) | ((t >> 4) & 0x30u) | ((t >> 8) & 0x300u) |
+                             ((t >> 12) & 0x3000u);
+        *bad |= __byte_perm(0x54474341u, 0u, sel) != v;  // 'A' 'C' 'G' 'T'
     }
+    return word;
 }
 
 // Pack the concatenated reads (bytes [base, base + total) of `reads`) into
 // 2-bit words, with kReadPadBases zero bases in front; flags non-ACGT bytes.
+// Two independent words per thread and iteration keep two 16-byte loads in flight.
 __global__ void k_pack_reads(const uint8_t* __restrict__ reads, uint64_t base, uint64_t total,
                              uint32_t* __restrict__ words, uint64_t nwords, int aligned16,
                              int* status) {
     constexpr uint64_t padw = kReadPadBases / 16;
-    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nwords;
-         w += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t word = 0;
-        bool bad = false;
-        if (w >= padw) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (uint64_t w0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w0 < nwords;
+         w0 += 2 * stride) {
+        uint32_t parts[2][4];
+        bool full[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint64_t w = w0 + u * stride;
             const uint64_t b0 = (w - padw) * 16;
-            const uint8_t* src = reads + base + b0;
-            if (b0 + 16 <= total && aligned16) {
-                const uint4 v = *reinterpret_cast<const uint4*>(src);
-                const uint32_t parts[4] = {v.x, v.y, v.z, v.w};
+            full[u] = w < nwords && w >= padw && b0 + 16 <= total && aligned16;
+            if (full[u]) {
+                const uint4 v = *reinterpret_cast<const uint4*>(reads + base + b0);
+                parts[u][0] = v.x;
+                parts[u][1] = v.y;
+                parts[u][2] = v.z;
+                parts[u][3] = v.w;
+            }
+        }
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const uint32_t ch = (parts[q] >> (8 * j)) & 0xffu;
-                        bad |= !is_acgt(ch);
-                        word |= code_of(ch) << (2 * (4 * q + j));
-                    }
-            } else {
+        for (int u = 0; u < 2; ++u) {
+            const uint64_t w = w0 + u * stride;
+            if (w >= nwords) continue;
+            uint32_t word = 0;
+            if (full[u]) {
+                word = pack16_ascii(parts[u], &bad);
+            } else if (w >= padw) {
+                const uint64_t b0 = (w - padw) * 16;
+                const uint8_t* src = reads + base + b0;
                 for (uint64_t j = 0; j < 16 && b0 + j < total; ++j) {
                     const uint32_t ch = src[j];
                     bad |= !is_acgt(ch);
                     word |= code_of(ch) << (2 * j);
                 }
             }
+            words[w] = word;
         }
-        words[w] = word;
-        if (bad) atomicOr(status, kStBadBase);
     }
+    if (bad) atomicOr(status, kStBadBase);
 }
 
 // Distribute the reads the warp kernel must take (the short-read bucket's
@@ -307,21 +378,21 @@ struct FusedArgs {
 struct WarpCounters {
     uint32_t seeds = 0, slot_reads = 0, list_entries = 0, ed_calls = 0, ed_over = 0;
     unsigned long long window_words = 0;
-    uint32_t ed_filtered = 0;
+    uint32_t ed_filtered = 0, reads_done = 0;
 };
 
 __device__ __forceinline__ void flush_counters(DevCounters* ctr, WarpCounters& c) {
-    unsigned long long v[7] = {c.seeds, c.slot_reads, c.list_entries, c.ed_calls, c.ed_over,
-                               c.window_words, c.ed_filtered};
+    unsigned long long v[8] = {c.seeds, c.slot_reads, c.list_entries, c.ed_calls, c.ed_over,
+                               c.window_words, c.ed_filtered, c.reads_done};
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < 8; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
     }
     if ((threadIdx.x & 31) == 0) {
         unsigned long long* dst = &ctr->seeds;
 #pragma unroll
-        for (int k = 0; k < 7; ++k)
+        for (int k = 0; k < 8; ++k)
             if (v[k]) atomicAdd(dst + k, v[k]);
     }
 }
@@ -995,6 +1066,7 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
         }
     }
     if (lane == 0) {
+        wc.reads_done++;
         // two 8-byte stores: snap_result arrays need only their natural alignment
         unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.out + r);
         dst[0] = (unsigned long long)res_loc;
@@ -1320,7 +1392,7 @@ int prepare_batch(const snap_index* idx, Engine* e, const uint8_t* d_reads,
     SNAP_CUDA(cudaEventRecord(e->ev[0], stream), "event");
     SNAP_CUDA(cudaMemsetAsync(d_st, 0, sizeof(BatchStats), stream), "stats clear");
     e->launches++;
-    k_read_stats<<<grid_cap(e->sms, n, 256), 256, 0, stream>>>(
+    k_read_stats<<<stats_grid(e->sms, n), kStatsThreads, 0, stream>>>(
         d_offsets, n, idx->s, idx->stride, p->num_seeds, p->max_dist, p->conf_diff, p->max_hits,
         p->max_dist_per_read, d_st);
     SNAP_CUDA(cudaGetLastError(), "stats launch");
@@ -1332,6 +1404,7 @@ int prepare_batch(const snap_index* idx, Engine* e, const uint8_t* d_reads,
     SNAP_CUDA(cudaMemcpyAsync(h_base, d_offsets, sizeof(uint64_t), cudaMemcpyDeviceToHost, stream),
               "offset copy");
     SNAP_CUDA(cudaStreamSynchronize(stream), where);
+    e->t_stats = std::chrono::steady_clock::now();
     out->st = *h_st;
     out->base0 = *h_base;
     if (out->st.status) return status_to_code(out->st.status, where);
@@ -1348,6 +1421,17 @@ int prepare_batch(const snap_index* idx, Engine* e, const uint8_t* d_reads,
     return SNAP_OK;
 }
 
+// Milliseconds between two recorded events, 0 when the runtime cannot tell; a
+// failure here is not left behind as the thread's last CUDA error.
+static double event_ms(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return ms;
+}
+
 static int finish_status(Engine* e, cudaStream_t stream, const char* where, uint64_t n) {
     BatchStats* d_st = static_cast<BatchStats*>(e->stats.p);
     SNAP_CUDA(cudaEventRecord(e->ev[3], stream), "event");
@@ -1358,16 +1442,11 @@ static int finish_status(Engine* e, cudaStream_t stream, const char* where, uint
     const int rc = status_to_code(h->status, where);
     if (rc) return rc;
     snap_call_stats& L = e->last;
-    float ms = 0;
     L.kernel_launches = e->launches;
-    cudaEventElapsedTime(&ms, e->ev[0], e->ev[1]);
-    L.stats_ms = ms;
-    cudaEventElapsedTime(&ms, e->ev[1], e->ev[2]);
-    L.pack_ms = ms;
-    cudaEventElapsedTime(&ms, e->ev[2], e->ev[3]);
-    L.align_ms = ms;
-    cudaEventElapsedTime(&ms, e->ev[0], e->ev[3]);
-    L.total_ms = ms;
+    L.stats_ms = event_ms(e->ev[0], e->ev[1]);
+    L.pack_ms = event_ms(e->ev[1], e->ev[2]);
+    L.align_ms = event_ms(e->ev[2], e->ev[3]);
+    L.total_ms = event_ms(e->ev[0], e->ev[3]);
     L.reads = n;
     L.read_bases = h->total_bases;
     L.seeds = h->ctr.seeds;
@@ -1383,11 +1462,19 @@ static int finish_status(Engine* e, cudaStream_t stream, const char* where, uint
     L.graph_replay = e->last_graph;
     L.team_classes = e->last_team;
     L.probe_ms = L.distance_ms = 0;
+    L.host_plan_ms = e->host_plan_ms;
+    L.reads_light = h->ctr_light.reads_done;
+    L.light_seeds = h->ctr_light.seeds;
+    L.light_slot_reads = h->ctr_light.slot_reads;
+    L.light_list_entries = h->ctr_light.list_entries;
+    L.light_ed_calls = h->ctr_light.ed_calls;
+    L.light_window_bytes = h->ctr_light.window_words * 4;
+    L.light_ms = 0;
+    if (e->last_light && h->light_end_ns > ~h->light_start_ns_neg)
+        L.light_ms = (double)(h->light_end_ns - ~h->light_start_ns_neg) * 1e-6;
     if (e->last_plain) {
-        cudaEventElapsedTime(&ms, e->pev[3], e->pev[0]);
-        L.probe_ms = ms;
-        cudaEventElapsedTime(&ms, e->pev[1], e->pev[2]);
-        L.distance_ms = ms;
+        L.probe_ms = event_ms(e->pev[3], e->pev[0]);
+        L.distance_ms = event_ms(e->pev[1], e->pev[2]);
     }
     return SNAP_OK;
 }
@@ -1712,6 +1799,7 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
         }
     e->last_team = 0;
     for (int q = 0; q < kClasses; ++q) e->last_team += plan.use[q] && is_team_kernel(plan.kfn[q]);
+    e->last_light = plan.light;
     e->last_graph = 0;
     if (e->use_graphs && stream != nullptr && stream != cudaStreamLegacy &&
         stream != cudaStreamPerThread) {
@@ -1781,12 +1869,15 @@ int align_batch_device(const snap_index* idx, Engine* e, const uint8_t* d_reads,
     e->last_shape = LaunchShape{0, 0, 0};  // set again by the batched form
     e->last_graph = 0;
     e->last_team = 0;
+    e->last_light = false;
     e->last_plain = plain;
     BatchPrep bp;
     if ((rc = prepare_batch(idx, e, d_reads, d_offsets, n, p, stream, &bp, where))) return rc;
     rc = plain ? align_plain(idx, e, d_offsets, n, p, d_out, stream, bp)
                : align_fused(idx, e, d_offsets, n, p, d_out, stream, bp);
     if (rc) return rc;
+    e->host_plan_ms = std::chrono::duration<double, std::milli>(
+                          std::chrono::steady_clock::now() - e->t_stats).count();
     return finish_status(e, stream, where, n);
 }
 
@@ -1989,7 +2080,7 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
     int sms = 0, dev = 0;
     SNAP_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     SNAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-    k_read_stats<<<grid_cap(sms, n, 256), 256, 0, stream>>>(
+    k_read_stats<<<stats_grid(sms, n), kStatsThreads, 0, stream>>>(
         d_offsets, n, idx->s, idx->stride, p->num_seeds, p->max_dist, p->conf_diff, p->max_hits,
         p->max_dist_per_read, d_st);
     SNAP_CUDA(cudaGetLastError(), "stats launch");

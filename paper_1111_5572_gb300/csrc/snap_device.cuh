@@ -390,6 +390,13 @@ __device__ __forceinline__ int lv_warp(const uint32_t* X, int m, const uint32_t*
     return lv_warp_smem(X, m, Tw, tb, n, L, lane, Ra, Rb);
 }
 
+// The device's global nanosecond clock.
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Warp-wide max of a 64-bit value.
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
 #pragma unroll

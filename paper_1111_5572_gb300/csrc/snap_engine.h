@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -41,6 +42,7 @@ struct Engine {
     PinnedBuf pin;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};  // plain-form stage marks
+    bool last_light = false;  // the thread-per-read kernel ran in the last call
     uint64_t launches = 0;
     snap_call_stats last{};
     // autotuner and graph replay of the batched form
@@ -54,6 +56,9 @@ struct Engine {
     int last_team = 0;  // classes of the last batch that ran in team mode
     int team = -1;      // team mode: -1 chosen per batch, 0 never, 1 always
     bool last_plain = false;  // the last call ran the plain form (pev marks are valid)
+    // host clock when the batch statistics arrived, and the planning time after it
+    std::chrono::steady_clock::time_point t_stats;
+    double host_plan_ms = 0;
     uint64_t overflow_budget = 4ull << 30;  // device bytes for per-warp global candidate tables
     // plain-form workspace
     DevBuf p_seeds, p_hits, p_hitoff, p_partial, p_table, p_events, p_hitlist, p_items, p_misc,

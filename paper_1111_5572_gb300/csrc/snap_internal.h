@@ -88,7 +88,7 @@ struct HitRec {
 // Traffic counters accumulated by the align kernels (one atomicAdd per warp).
 struct DevCounters {
     unsigned long long seeds, slot_reads, list_entries, ed_calls, ed_over, window_words,
-        ed_filtered;
+        ed_filtered, reads_done;
 };
 
 // Statistics of a read batch, computed on the device before the main launch.
@@ -99,7 +99,11 @@ struct BatchStats {
     int max_seeds;     // max over reads of n
     int status;
     unsigned long long max_hits_bound;  // max over reads of n * h_max (capped)
-    DevCounters ctr;
+    DevCounters ctr;        // every align kernel of the call (both forms)
+    DevCounters ctr_light;  // the thread-per-read kernel alone (also in ctr)
+    // device clock (ns) of the thread-per-read kernel: the latest block end, and the
+    // complement of the earliest block start (atomicMax of ~start is a min of start)
+    unsigned long long light_end_ns, light_start_ns_neg;
     unsigned long long n_light;  // reads short enough for the thread-per-read bucket
     // per read-length class (see kClassBounds): reads and the maxima that size a launch
     unsigned long long cls_n[4];

@@ -6,11 +6,12 @@
 // most 16 index positions; the thread then runs the whole per-read loop alone:
 // seed probes, votes in a small per-thread candidate list, the most-voted pick,
 // the limit schedule, a Landau-Vishkin edit distance over one diagonal at a time,
-// best / second best over 32-base buckets and the exits.  Any other read, and
-// any read whose edit distances would need a fifth round, is appended to a
-// device list that the warp-per-read kernel (snap_align.cu) drains next (from
-// scratch), so every result comes from exactly one of the two, with the same
-// readings of the paper (see snap_align.cu).
+// best / second best over 32-base buckets and the exits.  An edit distance that
+// would need a fifth round is computed by the whole warp (see k_align_light).
+// Any other read is appended to a device list that the warp-per-read kernel
+// (snap_align.cu) drains next, starting from the probe records written here, so
+// every result comes from exactly one of the two, with the same readings of the
+// paper (see snap_align.cu).
 //
 // Per-thread arrays live in shared memory in column order (word w of thread t at
 // w * blockDim + t) so that a warp's accesses to the same word fall in 32
@@ -28,14 +29,21 @@ constexpr int kLightMaxM = kLightBucketMaxM;
 constexpr int kLightMaxSeeds = kLightBucketMaxSeeds;
 constexpr int kLightMaxL = kLightBucketMaxL;
 constexpr int kLightMaxCands = 16;
-// A thread gives its read to the warp-per-read kernel rather than start edit
-// distance round 4 (16 diagonals done): the rare long distances would otherwise
-// hold the other 31 lanes of the warp idle.
+// A thread posts its distance to the warp rather than start edit distance round 4
+// (16 diagonals done): the rare long distances would otherwise hold the other 31
+// lanes of the warp idle.
 constexpr int kLightMaxRounds = 4;
 constexpr int kLightXW = kLightMaxM / 16 + 2;                           // read words + 2
 constexpr int kLightTW = (15 + kLightMaxM + kLightMaxL + 15) / 16 + 2;  // window words
 constexpr int kLightRW = 2 * (kLightMaxRounds - 1) + 3;                 // diagonals + 2
 constexpr int kLightWords = 2 * kLightXW + kLightTW + kLightRW;
+// per warp: a read strand and a window for the distances the warp computes together
+constexpr int kLightScratchWords = (kLightXW + kLightTW + 3) & ~3;
+
+// shared memory of a block of `threads` threads
+constexpr size_t light_smem_bytes(int threads) {
+    return ((size_t)kLightWords * threads + (size_t)(threads / 32) * kLightScratchWords) * 4;
+}
 
 namespace {
 
@@ -65,6 +73,8 @@ struct LightArgs {
     uint8_t* hprobed;  // per read: 1 when hseeds holds them
     int* status;
     DevCounters* ctr;
+    DevCounters* ctr_light;
+    BatchStats* stats;  // kernel start and end clocks
 };
 
 // 32 bases from a column-stored packed sequence (stride = threads per block)
@@ -78,21 +88,53 @@ __device__ __forceinline__ uint64_t col32(const uint32_t* col, int i, int st) {
 // VARIANT: the index has a stride > 1 or first_seeds > 1 (probe slots grouped
 // per seed, picks deferred); without it a probe is a seed and every non-popular
 // one picks, which keeps the common case's registers free.
+//
+// Each thread runs Algorithm 1 for its read until the read ends or an edit
+// distance would need a fifth round; it then posts that distance and waits.
+// When every thread of the warp has ended or posted, the warp computes the
+// posted distances one after another with all 32 lanes (one diagonal per lane)
+// and the posting threads resume where they stopped.  A long distance thus
+// costs the warp one warp-wide distance (its rounds run in parallel over the
+// diagonals) instead of one lane walking every diagonal in turn while 31 lanes
+// idle, and no read leaves the kernel because of its distances.
 template <bool VARIANT>
-__global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
+__global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int st = blockDim.x;  // column stride of the per-thread arrays
     uint32_t* Xf = smem + tid;
     uint32_t* Xr = Xf + kLightXW * st;
     uint32_t* Tw = Xr + kLightXW * st;
     int* R = reinterpret_cast<int*>(Tw + kLightTW * st);
+    // this warp's scratch for warp-wide distances: read strand, then window
+    uint32_t* wscr = smem + kLightWords * st + (tid >> 5) * kLightScratchWords;
     const uint64_t r = blockIdx.x * (uint64_t)st + tid;
+    if (tid == 0) atomicMax(&a.stats->light_start_ns_neg, ~globaltimer_ns());
 
-    uint32_t c_seeds = 0, c_slots = 0, c_list = 0, c_ed = 0, c_over = 0, c_words = 0;
+    uint32_t c_seeds = 0, c_slots = 0, c_list = 0, c_ed = 0, c_over = 0, c_words = 0, c_done = 0;
+    // the read and its Algorithm 1 state
+    int m = 0, n = 0, dmax = 0;
+    bool heavy = false;  // the warp-per-read kernel takes the read
+    bool live = false;   // Algorithm 1 still running here
+    SeedRec seeds[kLightMaxSeeds];
+    unsigned long long ckey[kLightMaxCands];
+    uint8_t cvotes[kLightMaxCands];
+    int8_t cstate[kLightMaxCands];
+    unsigned long long hkey[kLightMaxCands];
+    int8_t hd[kLightMaxCands];
+    int nc = 0, nh = 0, t = 0, voted = 0, i = 0, last_np = -1;
+    int d_best = kInfL, d_second = kInfL;
+    unsigned long long best_key = 0;
+    bool any_nonpopular = false, returned = false, draining = false;
+    int phase = 0;  // 0: next seed's votes, 1: pick and score, 2: exit tests
+    // a distance posted to the warp: the candidate, its limit, and the result
+    bool posted = false, resumed = false;
+    int pend_pick = 0, pend_L = 0, pend_d = 0;
+    const int c = a.c;
+
     if (r < a.n) {
         const uint64_t o0 = a.offsets[r];
-        const int m = (int)(a.offsets[r + 1] - o0);
+        m = (int)(a.offsets[r + 1] - o0);
         const int s = a.s;
         int ng = 0;  // seeds
         if (m >= s) {
@@ -100,12 +142,9 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
             ng = min(ng, m - s + 1);
         }
         const int stride = VARIANT ? a.stride : 1;
-        const int n = ng * stride;  // probe slots (stride-k index: k per seed)
-        const int dmax = a.dmax_per_read ? a.dmax_per_read[r] : a.d_max;
-        const int c = a.c;
-        bool heavy = m > kLightMaxM || n > kLightMaxSeeds || dmax + c - 1 > kLightMaxL;
-        long long res_loc = -1;
-        int res_d = -1, res_strand = 0, res_cls = SNAP_NOT_FOUND;
+        n = ng * stride;  // probe slots (stride-k index: k per seed)
+        dmax = a.dmax_per_read ? a.dmax_per_read[r] : a.d_max;
+        heavy = m > kLightMaxM || n > kLightMaxSeeds || dmax + c - 1 > kLightMaxL;
         if (!heavy && n > 0) {
             const uint64_t rb = o0 - a.base0 + kReadPadBases;
             const int nw = (m + 15) / 16;
@@ -129,13 +168,11 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                 Xr[w * st] = rc;
             }
             // seed lookups
-            SeedRec seeds[kLightMaxSeeds];
             unsigned H = 0;
-            int last_np = -1;  // last non-popular seed (seeds-first variant)
-            for (int i = 0; i < n; ++i) {
+            for (int q = 0; q < n; ++q) {
                 bool p0 = false;
-                const int o = VARIANT ? probe_offset(i, stride, m, s, a.shifts, a.n_shifts, &p0)
-                                      : seed_offset(i, m, s, a.shifts, a.n_shifts, &p0);
+                const int o = VARIANT ? probe_offset(q, stride, m, s, a.shifts, a.n_shifts, &p0)
+                                      : seed_offset(q, m, s, a.shifts, a.n_shifts, &p0);
                 SeedRec rec;
                 rec.pad = 0;
                 if (o < 0) {  // a probe that does not fit in the read
@@ -143,7 +180,7 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                     rec.offset = 0;
                     rec.fwd_n = rec.rc_n = 0;
                     rec.fwd_ref = rec.rc_ref = 0;
-                    seeds[i] = rec;
+                    seeds[q] = rec;
                     continue;
                 }
                 rec.flags = (uint8_t)(kSeedValid | (p0 ? kSeedPass0 : 0));
@@ -158,79 +195,93 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                     H += (unsigned)rec.fwd_n + rec.rc_n;
                     if (stride == 1) {  // a probe is a seed
                         rec.flags |= (uint8_t)(kSeedPick | (p0 ? kSeedCountT : 0));
-                        if (VARIANT) last_np = i;
+                        if (VARIANT) last_np = q;
                     }
                 }
-                seeds[i] = rec;
+                seeds[q] = rec;
             }
             if (VARIANT && stride > 1)  // per seed: its last non-popular probe picks
                 for (int g = 0; g < ng; ++g)
-                    last_np = max(last_np, mark_seed_group(g, a.stride, n, [&](int i) {
-                                      return &seeds[i].flags;
+                    last_np = max(last_np, mark_seed_group(g, a.stride, n, [&](int q) {
+                                      return &seeds[q].flags;
                                   }));
             heavy = H > (unsigned)kLightMaxCands;
-            if (!heavy) {
-                unsigned long long ckey[kLightMaxCands];
-                uint8_t cvotes[kLightMaxCands];
-                int8_t cstate[kLightMaxCands];
-                unsigned long long hkey[kLightMaxCands];
-                int8_t hd[kLightMaxCands];
-                int nc = 0, nh = 0, t = 0, voted = 0;
-                int d_best = kInfL, d_second = kInfL;
-                unsigned long long best_key = 0;
-                bool any_nonpopular = false, returned = false, draining = false;
-                bool gave_up = false;
-                int i = 0;
-                for (;;) {
-                    if (!draining) {
-                        while (i < n &&
-                               (seeds[i].flags & (kSeedValid | kSeedPopular)) != kSeedValid)
-                            ++i;
-                        if (i >= n) break;
-                        const SeedRec rec = seeds[i++];
-                        any_nonpopular = true;
-                        const int o = rec.offset;
-                        const int tot = (int)rec.fwd_n + rec.rc_n;
-                        for (int j = 0; j < tot; ++j) {
-                            const bool fwd = j < rec.fwd_n;
-                            uint32_t l;
-                            if (rec.flags & kSeedFwdInline) {
-                                l = fwd ? rec.fwd_ref : rec.rc_ref;
-                            } else {
-                                l = fwd ? __ldg(a.positions + rec.fwd_ref + j)
-                                        : __ldg(a.positions + rec.rc_ref + (j - rec.fwd_n));
-                                ++c_list;
-                            }
-                            const long long p =
-                                fwd ? (long long)l - o : (long long)l - (m - o - s);
-                            if (p < 0) continue;
-                            const unsigned long long key =
-                                2ull * (unsigned long long)p + (fwd ? 0 : 1);
-                            int q = 0;
-                            while (q < nc && ckey[q] != key) ++q;
-                            if (q == nc) {
-                                ckey[nc] = key;
-                                cvotes[nc] = 0;
-                                cstate[nc] = (int8_t)kUnscored;
-                                ++nc;
-                            }
-                            ++cvotes[q];
-                        }
-                        if (rec.flags & kSeedCountT) ++t;
-                        if (VARIANT) {
-                            if (!(rec.flags & kSeedPick)) continue;  // more probes of this seed
-                            // seeds-first variant: no pick before first_seeds non-popular
-                            // seeds (or all of them) have voted
-                            if (++voted < a.first_seeds && i <= last_np) continue;
-                        }
+            live = !heavy;
+            if (heavy && a.hseeds) {  // handed over after probing: the warp kernel
+                for (int q = 0; q < n; ++q)  // starts from these records
+                    a.hseeds[r * kLightMaxSeeds + q] = seeds[q];
+                a.hprobed[r] = 1;
+            }
+        }
+    }
+
+    for (;;) {
+        // this thread: Algorithm 1 until the read ends or posts a long distance
+        while (live && !posted) {
+            if (phase == 0) {
+                if (draining) {
+                    phase = 1;
+                } else {
+                    while (i < n && (seeds[i].flags & (kSeedValid | kSeedPopular)) != kSeedValid)
+                        ++i;
+                    if (i >= n) {
+                        live = false;
+                        break;
                     }
+                    const SeedRec rec = seeds[i++];
+                    any_nonpopular = true;
+                    const int o = rec.offset;
+                    const int tot = (int)rec.fwd_n + rec.rc_n;
+                    for (int j = 0; j < tot; ++j) {
+                        const bool fwd = j < rec.fwd_n;
+                        uint32_t l;
+                        if (rec.flags & kSeedFwdInline) {
+                            l = fwd ? rec.fwd_ref : rec.rc_ref;
+                        } else {
+                            l = fwd ? __ldg(a.positions + rec.fwd_ref + j)
+                                    : __ldg(a.positions + rec.rc_ref + (j - rec.fwd_n));
+                            ++c_list;
+                        }
+                        const long long p = fwd ? (long long)l - o : (long long)l - (m - o - a.s);
+                        if (p < 0) continue;
+                        const unsigned long long key = 2ull * (unsigned long long)p + (fwd ? 0 : 1);
+                        int q = 0;
+                        while (q < nc && ckey[q] != key) ++q;
+                        if (q == nc) {
+                            ckey[nc] = key;
+                            cvotes[nc] = 0;
+                            cstate[nc] = (int8_t)kUnscored;
+                            ++nc;
+                        }
+                        ++cvotes[q];
+                    }
+                    if (rec.flags & kSeedCountT) ++t;
+                    if (VARIANT) {
+                        if (!(rec.flags & kSeedPick)) continue;  // more probes of this seed
+                        // seeds-first variant: no pick before first_seeds non-popular
+                        // seeds (or all of them) have voted
+                        if (++voted < a.first_seeds && i <= last_np) continue;
+                    }
+                    phase = 1;
+                }
+            }
+            if (phase == 1) {
+                int pick = -1, d = kOver;
+                if (resumed) {  // the warp computed the distance this thread posted
+                    resumed = false;
+                    pick = pend_pick;
+                    d = pend_d;
+                } else {
                     // most-voted unscored candidate, ties to the smaller key
-                    int pick = -1;
                     for (int q = 0; q < nc; ++q) {
                         if (cstate[q] != kUnscored) continue;
                         if (pick < 0 || cvotes[q] > cvotes[pick] ||
                             (cvotes[q] == cvotes[pick] && ckey[q] < ckey[pick]))
                             pick = q;
+                    }
+                    if (pick < 0 && draining) {
+                        live = false;
+                        break;
                     }
                     if (pick >= 0) {
                         int L;
@@ -241,9 +292,8 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                         } else {
                             L = d_best - 1;
                         }
-                        const unsigned long long key = ckey[pick];
-                        int d = kOver;
                         if (L >= 0) {
+                            const unsigned long long key = ckey[pick];
                             const uint64_t p = key >> 1;
                             const int n_t = (int)min(a.G - p, (uint64_t)(m + L));
                             const uint64_t w0 = p >> 4;
@@ -253,51 +303,94 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                             c_words += nwt;
                             d = lv_lane((key & 1) ? Xr : Xf, st, m, Tw, st, tb, n_t, L, R, st,
                                         kLightMaxRounds);
-                            if (d == kLaneGaveUp) {
-                                gave_up = true;  // the warp-per-read kernel redoes this read
+                            if (d == kLaneGaveUp) {  // the warp computes it (window in Tw)
+                                posted = true;
+                                pend_pick = pick;
+                                pend_L = L;
                                 break;
                             }
                         }
-                        ++c_ed;
-                        c_over += (d < 0);
-                        cstate[pick] = (int8_t)(d >= 0 ? d : kOver);
-                        if (d >= 0) {
-                            hkey[nh] = key;
-                            hd[nh] = (int8_t)d;
-                            ++nh;
-                            const unsigned long long bk = ((key >> 6) << 1) | (key & 1);
-                            if (d < d_best) {
-                                d_best = d;
-                                best_key = key;
-                                d_second = kInfL;
-                                for (int q = 0; q < nh; ++q) {
-                                    const unsigned long long hb =
-                                        ((hkey[q] >> 6) << 1) | (hkey[q] & 1);
-                                    if (hb != bk) d_second = min(d_second, (int)hd[q]);
-                                }
-                            } else if (bk != (((best_key >> 6) << 1) | (best_key & 1))) {
-                                d_second = min(d_second, d);
-                            }
-                        }
-                    } else if (draining) {
-                        break;
-                    }
-                    if (!draining) {
-                        if (d_best < c && d_second < d_best + c) {
-                            returned = true;
-                            break;
-                        }
-                        if (t >= d_best + c) draining = true;
                     }
                 }
-                if (gave_up) {
-                    heavy = true;
-                } else if (!returned && d_best <= dmax && d_second >= d_best + c) {
+                if (pick >= 0) {
+                    const unsigned long long key = ckey[pick];
+                    ++c_ed;
+                    c_over += (d < 0);
+                    cstate[pick] = (int8_t)(d >= 0 ? d : kOver);
+                    if (d >= 0) {
+                        hkey[nh] = key;
+                        hd[nh] = (int8_t)d;
+                        ++nh;
+                        const unsigned long long bk = ((key >> 6) << 1) | (key & 1);
+                        if (d < d_best) {
+                            d_best = d;
+                            best_key = key;
+                            d_second = kInfL;
+                            for (int q = 0; q < nh; ++q) {
+                                const unsigned long long hb =
+                                    ((hkey[q] >> 6) << 1) | (hkey[q] & 1);
+                                if (hb != bk) d_second = min(d_second, (int)hd[q]);
+                            }
+                        } else if (bk != (((best_key >> 6) << 1) | (best_key & 1))) {
+                            d_second = min(d_second, d);
+                        }
+                    }
+                }
+                phase = 2;
+            }
+            if (phase == 2) {
+                if (!draining) {
+                    if (d_best < c && d_second < d_best + c) {
+                        returned = true;
+                        live = false;
+                        break;
+                    }
+                    if (t >= d_best + c) draining = true;
+                }
+                phase = 0;
+            }
+        }
+        // the warp: every posted distance, all lanes on each (limits are <= 15)
+        const unsigned pm = __ballot_sync(kFull, posted);
+        if (!pm) break;
+        for (unsigned mm = pm; mm; mm &= mm - 1) {
+            const int j = __ffs(mm) - 1;
+            const unsigned long long key = __shfl_sync(kFull, posted ? ckey[pend_pick] : 0ull, j);
+            const int L = __shfl_sync(kFull, pend_L, j);
+            const int mj = __shfl_sync(kFull, m, j);
+            const uint64_t p = key >> 1;
+            const int n_t = (int)min(a.G - p, (uint64_t)(mj + L));
+            const int tb = (int)(p & 15);
+            const int nwt = (tb + n_t + 15) / 16 + 2;
+            const int tj = tid - lane + j;  // column of lane j
+            const uint32_t* Xj = smem + ((key & 1) ? kLightXW * st : 0) + tj;
+            const uint32_t* Tj = smem + 2 * kLightXW * st + tj;  // its window is still there
+            for (int w = lane; w < kLightXW + nwt; w += 32)
+                wscr[w] = w < kLightXW ? Xj[w * st] : Tj[(w - kLightXW) * st];
+            __syncwarp();
+            const int d = lv_warp_reg<1>(wscr, mj, wscr + kLightXW, tb, n_t, L, lane);
+            __syncwarp();
+            if (lane == j) {
+                pend_d = d;
+                posted = false;
+                resumed = true;
+            }
+        }
+    }
+
+    if (r < a.n) {
+        if (heavy) {
+            const unsigned long long at = atomicAdd(a.heavy_count, 1ull);
+            a.heavy_ids[at] = (uint32_t)r;
+        } else {
+            ++c_done;
+            long long res_loc = -1;
+            int res_d = -1, res_strand = 0, res_cls = SNAP_NOT_FOUND;
+            if (n > 0) {
+                if (!returned && d_best <= dmax && d_second >= d_best + c) {
                     res_cls = SNAP_SINGLE_HIT;
                 } else if (returned || d_best <= dmax || !any_nonpopular) {
                     res_cls = SNAP_MULTIPLE_HITS;
-                } else {
-                    res_cls = SNAP_NOT_FOUND;
                 }
                 if (res_cls != SNAP_NOT_FOUND && d_best <= dmax) {
                     res_loc = (long long)(best_key >> 1);
@@ -305,17 +398,6 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                     res_d = d_best;
                 }
             }
-            if (heavy && a.hseeds) {  // handed over after probing: the warp kernel
-                for (int i = 0; i < n; ++i)  // starts from these records
-                    a.hseeds[r * kLightMaxSeeds + i] = seeds[i];
-                a.hprobed[r] = 1;
-            }
-        }
-        if (heavy) {
-            const unsigned long long at = atomicAdd(a.heavy_count, 1ull);
-            a.heavy_ids[at] = (uint32_t)r;
-
-        } else {
             unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.out + r);
             dst[0] = (unsigned long long)res_loc;
             dst[1] = (unsigned long long)(uint32_t)res_d |
@@ -323,27 +405,34 @@ __global__ void __launch_bounds__(256) k_align_light(LightArgs a) {
                       << 32);
         }
     }
-    unsigned long long v[6] = {c_seeds, c_slots, c_list, c_ed, c_over, c_words};
+    // seeds, slot_reads, list_entries, ed_calls, ed_over, window_words, -, reads_done
+    unsigned long long v[8] = {c_seeds, c_slots, c_list, c_ed, c_over, c_words, 0, c_done};
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < 8; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
     }
-    if ((tid & 31) == 0) {
+    if (lane == 0) {
         unsigned long long* dst = &a.ctr->seeds;
+        unsigned long long* dl = &a.ctr_light->seeds;
 #pragma unroll
-        for (int k = 0; k < 6; ++k)
-            if (v[k]) atomicAdd(dst + k, v[k]);
+        for (int k = 0; k < 8; ++k)
+            if (v[k]) {
+                atomicAdd(dst + k, v[k]);
+                atomicAdd(dl + k, v[k]);
+            }
     }
+    __syncthreads();
+    if (tid == 0) atomicMax(&a.stats->light_end_ns, globaltimer_ns());
 }
 
 }  // namespace
 
 // Shared-memory limit of the thread-per-read kernel, set once (before any capture).
 int light_prepare() {
-    int rc = raise_smem_limit((const void*)k_align_light<false>, (size_t)kLightWords * 256 * 4);
+    int rc = raise_smem_limit((const void*)k_align_light<false>, light_smem_bytes(256));
     if (rc) return rc;
-    return raise_smem_limit((const void*)k_align_light<true>, (size_t)kLightWords * 256 * 4);
+    return raise_smem_limit((const void*)k_align_light<true>, light_smem_bytes(256));
 }
 
 // Launch the thread-per-read bucket over all n reads; reads it does not take
@@ -380,8 +469,10 @@ int launch_light(const snap_index* idx, Engine* e, const uint64_t* d_offsets, ui
     BatchStats* d_st = static_cast<BatchStats*>(e->stats.p);
     a.status = &d_st->status;
     a.ctr = &d_st->ctr;
+    a.ctr_light = &d_st->ctr_light;
+    a.stats = d_st;
     if (threads != 64 && threads != 128 && threads != 256) threads = 128;
-    const size_t smem = (size_t)kLightWords * threads * 4;
+    const size_t smem = light_smem_bytes(threads);
     SNAP_CUDA(cudaMemsetAsync(heavy_count, 0, sizeof(unsigned long long), stream), "clear");
     const uint64_t blocks = (n + threads - 1) / threads;
     e->launches++;
