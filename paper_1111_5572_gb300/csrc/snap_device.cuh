@@ -390,6 +390,30 @@ __device__ __forceinline__ int lv_warp(const uint32_t* X, int m, const uint32_t*
     return lv_warp_smem(X, m, Tw, tb, n, L, lane, Ra, Rb);
 }
 
+// Words [w0, w0 + nw) of `src` (nw <= 13; src 16-byte aligned) into the column
+// dst[0], dst[st], ... with the 16-byte chunks that cover them loaded first, all
+// at once, so the copy costs one memory round trip rather than one per word.
+// The chunks end at most 3 words past w0 + nw - 1 (callers' arrays are padded).
+__device__ __forceinline__ void load_words_col(uint32_t* dst, int st, const uint32_t* src,
+                                               uint64_t w0, int nw) {
+    const uint64_t a0 = w0 & ~3ull;
+    const int sh = (int)(w0 - a0);
+    const int nchunks = (sh + nw + 3) >> 2;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + a0);
+    uint4 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = j < nchunks ? __ldg(s4 + j) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t wj[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = 4 * j + q - sh;
+            if (k >= 0 && k < nw) dst[k * st] = wj[q];
+        }
+    }
+}
+
 // The device's global nanosecond clock.
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;

@@ -89,14 +89,17 @@ __device__ __forceinline__ uint64_t col32(const uint32_t* col, int i, int st) {
 // per seed, picks deferred); without it a probe is a seed and every non-popular
 // one picks, which keeps the common case's registers free.
 //
-// Each thread runs Algorithm 1 for its read until the read ends or an edit
-// distance would need a fifth round; it then posts that distance and waits.
-// When every thread of the warp has ended or posted, the warp computes the
-// posted distances one after another with all 32 lanes (one diagonal per lane)
-// and the posting threads resume where they stopped.  A long distance thus
-// costs the warp one warp-wide distance (its rounds run in parallel over the
-// diagonals) instead of one lane walking every diagonal in turn while 31 lanes
-// idle, and no read leaves the kernel because of its distances.
+// A thread first does everything that touches memory: its read, its seed
+// probes, the candidates its non-popular seeds vote for (at most 16), and for
+// each candidate an edit distance at the read's largest limit L0 = d_max + c - 1
+// stopped before a fifth round.  It then runs Algorithm 1 on those results: the
+// pick order depends only on the votes, and a distance at any limit L <= L0
+// follows from the one at L0 (exact when d <= L, else over), so a candidate
+// whose speculative distance came out exact needs no further work.  A candidate
+// that needed a fifth round is over for any L <= 3; for a larger L the thread
+// posts it and waits.  When every thread of the warp has ended or posted, the
+// warp computes the posted distances one after another with all 32 lanes (one
+// diagonal per lane) and the posting threads resume where they stopped.
 template <bool VARIANT>
 __global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
     extern __shared__ __align__(16) uint32_t smem[];
@@ -117,9 +120,16 @@ __global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
     bool heavy = false;  // the warp-per-read kernel takes the read
     bool live = false;   // Algorithm 1 still running here
     SeedRec seeds[kLightMaxSeeds];
+    // candidates: key 2p + strand, the distance at L0 found up front (exact d,
+    // kOver, or kLaneGaveUp when it needs a fifth round), votes, and the state
+    // Algorithm 1 gave it (kUnscored, kOver or the distance)
     unsigned long long ckey[kLightMaxCands];
+    int8_t csd[kLightMaxCands];
     uint8_t cvotes[kLightMaxCands];
     int8_t cstate[kLightMaxCands];
+    // votes in seed order: the candidate of every vote, and where each probe slot's end
+    uint8_t evc[kLightMaxCands];
+    uint8_t evend[kLightMaxSeeds];
     unsigned long long hkey[kLightMaxCands];
     int8_t hd[kLightMaxCands];
     int nc = 0, nh = 0, t = 0, voted = 0, i = 0, last_np = -1;
@@ -155,7 +165,7 @@ __global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
             const uint64_t xe = rb + (uint64_t)m;
             const int dq = (int)((xe >> 4) - q0);
             const uint32_t shx = (uint32_t)(xe & 15) * 2u;
-            for (int j = 0; j <= nw + 1; ++j) Tw[j * st] = a.rwords[q0 - 1 + j];
+            load_words_col(Tw, st, a.rwords, q0 - 1, nw + 2);
 #pragma unroll
             for (int w = 0; w < kLightXW; ++w) {
                 uint32_t f = 0, rc = 0;
@@ -206,11 +216,62 @@ __global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
                                       return &seeds[q].flags;
                                   }));
             heavy = H > (unsigned)kLightMaxCands;
-            live = !heavy;
             if (heavy && a.hseeds) {  // handed over after probing: the warp kernel
                 for (int q = 0; q < n; ++q)  // starts from these records
                     a.hseeds[r * kLightMaxSeeds + q] = seeds[q];
                 a.hprobed[r] = 1;
+            }
+            if (!heavy) {
+                // the votes of every non-popular seed, in seed order, and the
+                // distinct candidates they name
+                int ne = 0;
+                for (int q = 0; q < n; ++q) {
+                    const SeedRec rec = seeds[q];
+                    if ((rec.flags & (kSeedValid | kSeedPopular)) == kSeedValid) {
+                        const int o = rec.offset;
+                        const int tot = (int)rec.fwd_n + rec.rc_n;
+                        for (int j = 0; j < tot; ++j) {
+                            const bool fwd = j < rec.fwd_n;
+                            uint32_t l;
+                            if (rec.flags & kSeedFwdInline) {
+                                l = fwd ? rec.fwd_ref : rec.rc_ref;
+                            } else {
+                                l = fwd ? __ldg(a.positions + rec.fwd_ref + j)
+                                        : __ldg(a.positions + rec.rc_ref + (j - rec.fwd_n));
+                                ++c_list;
+                            }
+                            const long long p =
+                                fwd ? (long long)l - o : (long long)l - (m - o - s);
+                            if (p < 0) continue;
+                            const unsigned long long key =
+                                2ull * (unsigned long long)p + (fwd ? 0 : 1);
+                            int k = 0;
+                            while (k < nc && ckey[k] != key) ++k;
+                            if (k == nc) {
+                                ckey[nc] = key;
+                                cvotes[nc] = 0;
+                                cstate[nc] = (int8_t)kUnscored;
+                                ++nc;
+                            }
+                            evc[ne++] = (uint8_t)k;
+                        }
+                    }
+                    evend[q] = (uint8_t)ne;
+                }
+                // every candidate's distance at L0, at most four rounds
+                const int L0 = dmax + c - 1;
+                for (int k = 0; k < nc; ++k) {
+                    const unsigned long long key = ckey[k];
+                    const uint64_t p = key >> 1;
+                    const int n_t = (int)min(a.G - p, (uint64_t)(m + L0));
+                    const int tb = (int)(p & 15);
+                    const int nwt = (tb + n_t + 15) / 16 + 2;
+                    load_words_col(Tw, st, a.genome, p >> 4, nwt);
+                    c_words += nwt;
+                    csd[k] = (int8_t)lv_lane((key & 1) ? Xr : Xf, st, m, Tw, st, tb, n_t, L0, R, st,
+                                             kLightMaxRounds);
+                }
+                live = true;
             }
         }
     }
@@ -228,36 +289,13 @@ __global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
                         live = false;
                         break;
                     }
-                    const SeedRec rec = seeds[i++];
+                    const uint8_t flags = seeds[i].flags;
+                    for (int e = i > 0 ? evend[i - 1] : 0; e < evend[i]; ++e) ++cvotes[evc[e]];
+                    ++i;
                     any_nonpopular = true;
-                    const int o = rec.offset;
-                    const int tot = (int)rec.fwd_n + rec.rc_n;
-                    for (int j = 0; j < tot; ++j) {
-                        const bool fwd = j < rec.fwd_n;
-                        uint32_t l;
-                        if (rec.flags & kSeedFwdInline) {
-                            l = fwd ? rec.fwd_ref : rec.rc_ref;
-                        } else {
-                            l = fwd ? __ldg(a.positions + rec.fwd_ref + j)
-                                    : __ldg(a.positions + rec.rc_ref + (j - rec.fwd_n));
-                            ++c_list;
-                        }
-                        const long long p = fwd ? (long long)l - o : (long long)l - (m - o - a.s);
-                        if (p < 0) continue;
-                        const unsigned long long key = 2ull * (unsigned long long)p + (fwd ? 0 : 1);
-                        int q = 0;
-                        while (q < nc && ckey[q] != key) ++q;
-                        if (q == nc) {
-                            ckey[nc] = key;
-                            cvotes[nc] = 0;
-                            cstate[nc] = (int8_t)kUnscored;
-                            ++nc;
-                        }
-                        ++cvotes[q];
-                    }
-                    if (rec.flags & kSeedCountT) ++t;
+                    if (flags & kSeedCountT) ++t;
                     if (VARIANT) {
-                        if (!(rec.flags & kSeedPick)) continue;  // more probes of this seed
+                        if (!(flags & kSeedPick)) continue;  // more probes of this seed
                         // seeds-first variant: no pick before first_seeds non-popular
                         // seeds (or all of them) have voted
                         if (++voted < a.first_seeds && i <= last_np) continue;
@@ -272,12 +310,13 @@ __global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
                     pick = pend_pick;
                     d = pend_d;
                 } else {
-                    // most-voted unscored candidate, ties to the smaller key
-                    for (int q = 0; q < nc; ++q) {
-                        if (cstate[q] != kUnscored) continue;
-                        if (pick < 0 || cvotes[q] > cvotes[pick] ||
-                            (cvotes[q] == cvotes[pick] && ckey[q] < ckey[pick]))
-                            pick = q;
+                    // most-voted unscored candidate, ties to the smaller key (a
+                    // candidate exists once some seed has voted for it)
+                    for (int k = 0; k < nc; ++k) {
+                        if (cstate[k] != kUnscored || cvotes[k] == 0) continue;
+                        if (pick < 0 || cvotes[k] > cvotes[pick] ||
+                            (cvotes[k] == cvotes[pick] && ckey[k] < ckey[pick]))
+                            pick = k;
                     }
                     if (pick < 0 && draining) {
                         live = false;
@@ -292,23 +331,19 @@ __global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
                         } else {
                             L = d_best - 1;
                         }
-                        if (L >= 0) {
-                            const unsigned long long key = ckey[pick];
-                            const uint64_t p = key >> 1;
-                            const int n_t = (int)min(a.G - p, (uint64_t)(m + L));
-                            const uint64_t w0 = p >> 4;
-                            const int tb = (int)(p & 15);
-                            const int nwt = (tb + n_t + 15) / 16 + 2;
-                            for (int w = 0; w < nwt; ++w) Tw[w * st] = __ldg(a.genome + w0 + w);
-                            c_words += nwt;
-                            d = lv_lane((key & 1) ? Xr : Xf, st, m, Tw, st, tb, n_t, L, R, st,
-                                        kLightMaxRounds);
-                            if (d == kLaneGaveUp) {  // the warp computes it (window in Tw)
-                                posted = true;
-                                pend_pick = pick;
-                                pend_L = L;
-                                break;
-                            }
+                        // the distance at L from the one found at L0 >= L
+                        const int sd = csd[pick];
+                        if (L < 0) {
+                            d = kOver;
+                        } else if (sd >= 0) {
+                            d = sd <= L ? sd : kOver;
+                        } else if (sd == kOver || L < kLightMaxRounds) {
+                            d = kOver;  // over at L0, or needs more than L rounds
+                        } else {        // needs a fifth round: the warp computes it
+                            posted = true;
+                            pend_pick = pick;
+                            pend_L = L;
+                            break;
                         }
                     }
                 }
@@ -326,10 +361,10 @@ __global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
                             d_best = d;
                             best_key = key;
                             d_second = kInfL;
-                            for (int q = 0; q < nh; ++q) {
+                            for (int k = 0; k < nh; ++k) {
                                 const unsigned long long hb =
-                                    ((hkey[q] >> 6) << 1) | (hkey[q] & 1);
-                                if (hb != bk) d_second = min(d_second, (int)hd[q]);
+                                    ((hkey[k] >> 6) << 1) | (hkey[k] & 1);
+                                if (hb != bk) d_second = min(d_second, (int)hd[k]);
                             }
                         } else if (bk != (((best_key >> 6) << 1) | (best_key & 1))) {
                             d_second = min(d_second, d);
@@ -362,11 +397,11 @@ __global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
             const int n_t = (int)min(a.G - p, (uint64_t)(mj + L));
             const int tb = (int)(p & 15);
             const int nwt = (tb + n_t + 15) / 16 + 2;
-            const int tj = tid - lane + j;  // column of lane j
-            const uint32_t* Xj = smem + ((key & 1) ? kLightXW * st : 0) + tj;
-            const uint32_t* Tj = smem + 2 * kLightXW * st + tj;  // its window is still there
+            const uint32_t* Xj = smem + ((key & 1) ? kLightXW * st : 0) + (tid - lane + j);
+            const uint32_t* gw = a.genome + (p >> 4);
             for (int w = lane; w < kLightXW + nwt; w += 32)
-                wscr[w] = w < kLightXW ? Xj[w * st] : Tj[(w - kLightXW) * st];
+                wscr[w] = w < kLightXW ? Xj[w * st] : __ldg(gw + (w - kLightXW));
+            if (lane == 0) c_words += nwt;
             __syncwarp();
             const int d = lv_warp_reg<1>(wscr, mj, wscr + kLightXW, tb, n_t, L, lane);
             __syncwarp();
