@@ -103,6 +103,26 @@ def test_c3_uneven_lengths_scaled(snap, plain):
 
 
 @pytest.mark.parametrize("plain", [False, True])
+def test_c3_uneven_lengths_40Mbp_50k(snap, plain):
+    """The C3 recipe at 40 Mbp with 50,000 reads: enough reads per length class that
+    the batch-size-driven launch choices (warp per read for every class, the tuned
+    shape) are those of the full 400 Mbp / 2M-read batch."""
+    w = synth.CONFIGS["C3"].scaled(G=40_000_000, n_reads=50_000)
+    g, _ = w.make_genome()
+    rd = w.make_reads(g)
+    dpr = w.max_dist_per_read(rd.lengths())
+    params = w.params()
+    gi = snap.Index(g, w.seed_len)
+    got = gi.align(rd.bases, rd.offsets, max_dist_per_read=dpr, plain=plain, **params)
+    if not plain:
+        assert gi.last_call_stats()["team_classes"] == 0
+    ref, st = oracle.Index(g, w.seed_len).align(rd.bases, rd.offsets, max_dist_per_read=dpr,
+                                                threads=16, **params)
+    assert_same(got, ref, f"C3 40 Mbp plain={plain}")
+    assert st.n_single > 30_000
+
+
+@pytest.mark.parametrize("plain", [False, True])
 def test_c4_long_reads_scaled(snap, plain):
     # lengths: 80% 100 bp, 20% log-uniform [1000, 10000]; d_max = max(8, ceil(0.08 m))
     # reaches 800, which takes the shared-memory diagonal path of the edit distance
