@@ -184,20 +184,33 @@ int snap_align_plain_device(const snap_index* index, const uint8_t* d_reads,
  * must not stall the device (cudaMalloc/cudaFree can synchronize it), or a
  * process that routes every device allocation through its own allocator.
  *
- * All scratch (batch statistics, status word, queue head, packed reads,
- * candidate tables that do not fit in shared memory) lives in one fixed 64 MiB
- * array that every GPU loading the library holds until the process exits.
- * Limits: at most 201,326,432 read bases per call (the reads are packed 4 per
- * byte into 48 MiB), and seeds x max_hits per read small enough for one warp's
- * candidate table to fit in the remaining 16 MiB.  Larger batches fail with
- * SNAP_E_INVAL before any read is touched; split them.  The caller still
- * passes (and owns) the reads, offsets and results, as for snap_align_device.
+ * All scratch (batch statistics, status word, queue heads, packed reads, a list
+ * of deferred reads, candidate tables that do not fit in shared memory) lives in
+ * one fixed 64 MiB array that every GPU loading the library holds until the
+ * process exits, whether or not this entry point is ever called.  A call runs two
+ * launches: the first fills every SM and aligns each read whose candidate table
+ * fits in shared memory; a read whose candidates outgrow it is listed and aligned
+ * by the second launch, one table per warp in the array.  The results are those
+ * of snap_align_device.
+ *
+ * Errors: those of snap_align_device, and SNAP_E_INVAL, before any read is
+ * aligned, for
+ *   - more than 201,326,432 read bases in the call (the reads are packed 4 per
+ *     byte into 48 MiB): split the batch;
+ *   - a seeds x max_hits bound above 262,144 for some read (one warp's table
+ *     must fit in the array's 14 MiB of tables), e.g. reads longer than about
+ *     17 kb at max_hits 300 with num_seeds = 0;
+ * and SNAP_E_INVAL after the first launch when more than 524,288 reads of the
+ * call need a table larger than shared memory (split the batch).  The caller
+ * still passes (and owns) the reads, offsets and results, as for
+ * snap_align_device.
  *
  * The first call on a device looks up the array's device address and caches
  * it; make that first call before any stream capture on that device.  Every
- * call reuses the same array, so calls whose GPU work overlaps (other streams,
- * other threads) race with each other: keep them ordered.  Same arguments,
- * results and errors as snap_align_device.
+ * call synchronizes `stream` (it reads the batch statistics and the count of
+ * deferred reads back) and returns once the results are in d_out.  Every call
+ * reuses the same array, so calls whose GPU work overlaps (other streams, other
+ * threads) race with each other: keep them ordered.
  */
 int snap_align_device_noalloc(const snap_index* index, const uint8_t* d_reads,
                               const uint64_t* d_offsets, uint64_t n_reads,

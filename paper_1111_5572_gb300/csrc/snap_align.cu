@@ -364,6 +364,12 @@ struct FusedArgs {
     uint32_t* gqbits; // per-warp q-gram bitmaps (2 x kQWords) for large limits, or NULL
     const SeedRec* hseeds;   // probe records of reads handed over by the short-read
     const uint8_t* hprobed;  // bucket (kLightBucketMaxSeeds per read), flagged per read
+    // when set, a read whose candidate table fits in no table this launch has is
+    // listed here (defer_cap entries at most) instead of aligned; a later launch
+    // aligns the listed reads (the allocation-free entry point)
+    uint32_t* defer_ids;
+    unsigned long long* defer_count;
+    unsigned long long defer_cap;
     int* status;
     DevCounters* ctr;
     // per-warp shared-memory layout, in 32-bit words; every section offset is a
@@ -740,6 +746,7 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
     const int c = a.c;
     long long res_loc = -1;
     int res_d = -1, res_strand = 0, res_cls = SNAP_NOT_FOUND;
+    bool deferred = false;  // listed for a later launch (see FusedArgs::defer_ids)
 
     if (n > 0) {
         // ---- read and reverse complement, 2 bits per base ----
@@ -835,7 +842,18 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
             hits = nullptr;
             dense = nullptr;
             ok = false;
-            if (lane == 0) atomicOr(a.status, kStTableFull);
+            if (a.defer_ids) {  // aligned by a later launch that has the tables
+                deferred = true;
+                if (lane == 0) {
+                    const unsigned long long at = atomicAdd(a.defer_count, 1ull);
+                    if (at < a.defer_cap)
+                        a.defer_ids[at] = (uint32_t)r;
+                    else
+                        atomicOr(a.status, kStTableFull);
+                }
+            } else if (lane == 0) {
+                atomicOr(a.status, kStTableFull);
+            }
         }
         if (ok) {
             int nd = 0;        // distinct candidates so far (slots listed in dense)
@@ -1065,7 +1083,7 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
             __syncwarp();
         }
     }
-    if (lane == 0) {
+    if (lane == 0 && !deferred) {
         wc.reads_done++;
         // two 8-byte stores: snap_result arrays need only their natural alignment
         unsigned long long* dst = reinterpret_cast<unsigned long long*>(a.out + r);
@@ -2008,17 +2026,28 @@ extern "C" int snap_align_plain_device(const snap_index* idx, const uint8_t* d_r
 // fail or fragment it), a serving thread that must never stall (cudaMalloc and
 // cudaFree can synchronize the whole device), or a process whose device memory
 // is audited through its own allocator.  For them this entry point keeps every
-// piece of scratch (batch statistics, status word, queue head, packed reads and
-// the per-warp candidate tables that do not fit in shared memory) in one
-// file-scope device array of fixed size that is created when the library's
-// code is loaded onto a device and lives until the process exits.
+// piece of scratch (batch statistics, status word, queue heads, packed reads,
+// the list of reads deferred to the second launch and the candidate tables that
+// do not fit in shared memory) in one file-scope device array of fixed size that
+// is created when the library's code is loaded onto a device and lives until the
+// process exits.  The first launch fills every SM with warps that use shared-
+// memory tables only and lists the rare read whose candidates outgrow them; a
+// second launch aligns just the listed reads, one global table per warp.
 // ---------------------------------------------------------------------------
 namespace snapgpu {
 
 constexpr size_t kNoAllocBytes = 64ull << 20;      // whole array: 64 MiB per device
-constexpr size_t kNoAllocHeadBytes = 4096;         // statistics, status, counters, queue head
+constexpr size_t kNoAllocHeadBytes = 4096;         // statistics, status, counters, queue heads
 constexpr size_t kNoAllocReadBytes = 48ull << 20;  // packed reads (4 bases per byte)
-constexpr size_t kNoAllocTableBytes = kNoAllocBytes - kNoAllocHeadBytes - kNoAllocReadBytes;
+constexpr size_t kNoAllocDeferIds = 1u << 19;      // reads listed for the second launch
+constexpr size_t kNoAllocTableBytes =
+    kNoAllocBytes - kNoAllocHeadBytes - kNoAllocReadBytes - kNoAllocDeferIds * 4;
+// head region: batch statistics, then at kNoAllocQueueOff the two launches' queue
+// heads and the count of listed reads
+constexpr size_t kNoAllocQueueOff = 1024;
+static_assert(sizeof(BatchStats) <= kNoAllocQueueOff, "statistics overlap the queue heads");
+static_assert(kNoAllocQueueOff + 3 * sizeof(unsigned long long) <= kNoAllocHeadBytes,
+              "queue heads past the head region");
 constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -2070,13 +2099,15 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
     if ((rc = noalloc_scratch(&base))) return rc;
     unsigned char* b = static_cast<unsigned char*>(base);
     BatchStats* d_st = reinterpret_cast<BatchStats*>(b);
-    unsigned long long* d_head = reinterpret_cast<unsigned long long*>(b + 1024);
+    unsigned long long* d_q = reinterpret_cast<unsigned long long*>(b + kNoAllocQueueOff);
+    // d_q[0]: queue head of the first launch, [1]: of the second, [2]: reads listed
     uint32_t* d_words = reinterpret_cast<uint32_t*>(b + kNoAllocHeadBytes);
-    unsigned char* d_tables = b + kNoAllocHeadBytes + kNoAllocReadBytes;
+    uint32_t* d_defer = reinterpret_cast<uint32_t*>(b + kNoAllocHeadBytes + kNoAllocReadBytes);
+    unsigned char* d_tables = b + kNoAllocHeadBytes + kNoAllocReadBytes + kNoAllocDeferIds * 4;
 
     // the array keeps the previous call's contents: clear what must start at zero
     SNAP_CUDA(cudaMemsetAsync(d_st, 0, sizeof(BatchStats), stream), "clear statistics");
-    SNAP_CUDA(cudaMemsetAsync(d_head, 0, sizeof(unsigned long long), stream), "clear head");
+    SNAP_CUDA(cudaMemsetAsync(d_q, 0, 3 * sizeof(unsigned long long), stream), "clear heads");
     int sms = 0, dev = 0;
     SNAP_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     SNAP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
@@ -2100,10 +2131,6 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
                                        15));
         return SNAP_E_INVAL;
     }
-    const int aligned = ((reinterpret_cast<uintptr_t>(d_reads) + base0) % 16) == 0;
-    k_pack_reads<<<grid_cap(sms, nwords, 256), 256, 0, stream>>>(
-        d_reads, base0, hs.total_bases, d_words, nwords, aligned, &d_st->status);
-    SNAP_CUDA(cudaGetLastError(), "pack launch");
 
     FusedArgs a;
     memset(&a, 0, sizeof(a));
@@ -2118,7 +2145,7 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
     a.base0 = base0;
     a.order = nullptr;
     a.n_items = n;
-    a.head = d_head;
+    a.head = d_q;
     a.d_max = p->max_dist;
     a.h_max = p->max_hits;
     a.c = p->conf_diff;
@@ -2164,9 +2191,6 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
     SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem),
               "occupancy");
     if (per_sm < 1) per_sm = 1;
-    uint64_t blocks = (uint64_t)sms * per_sm;
-    const uint64_t need_blocks = (n + warps - 1) / warps;
-    if (blocks > need_blocks) blocks = need_blocks;
     uint64_t gcap = 64;
     while (gcap < 2 * hs.max_hits_bound) gcap <<= 1;
     if (gcap > kMaxTableSlots) {
@@ -2174,39 +2198,70 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
                   (unsigned long long)hs.max_hits_bound, kMaxTableSlots / 2);
         return SNAP_E_INVAL;
     }
-    if (gcap > (uint64_t)scap) {
-        // per-warp tables in the array; fewer warps when they would not fit
-        const uint64_t per_warp = gcap * (sizeof(CandSlot) + sizeof(HitRec) / 2 + 2);
-        const uint64_t max_warps = kNoAllocTableBytes / per_warp;
-        if (max_warps < 1) {
-            set_error("%s: seeds x max_hits per read (%llu) needs %llu bytes of candidate "
-                      "table, more than the %llu this entry point holds",
-                      where, (unsigned long long)hs.max_hits_bound,
-                      (unsigned long long)per_warp, (unsigned long long)kNoAllocTableBytes);
-            return SNAP_E_INVAL;
-        }
-        if (blocks * warps > max_warps) {
-            if (max_warps < (uint64_t)warps) {
-                // fewer warps per block; each warp keeps the same shared-memory layout
-                warps = (int)max_warps;
-                const size_t smem_w = (size_t)warps * a.warp_words * 4;
-                if ((rc = raise_smem_limit((const void*)kfn, (size_t)(int)smem_w))) return rc;
-            }
-            blocks = std::max<uint64_t>(1, max_warps / warps);
-        }
-        const uint64_t tw = blocks * warps;
-        a.gtab = reinterpret_cast<CandSlot*>(d_tables);
-        a.ghits = reinterpret_cast<HitRec*>(d_tables + tw * gcap * sizeof(CandSlot));
-        a.gdense = reinterpret_cast<uint32_t*>(d_tables + tw * gcap * sizeof(CandSlot) +
-                                               tw * (gcap / 2) * sizeof(HitRec));
-        a.gcap = (uint32_t)gcap;
-        // the array keeps the previous call's contents: empty the tables this call uses
-        k_init_ctab<<<grid_cap(sms, tw * gcap, 256), 256, 0, stream>>>(a.gtab, tw * gcap);
-        SNAP_CUDA(cudaGetLastError(), "table init");
+    // global table of one warp (slots, hits, dense list) for the reads that need one
+    const uint64_t per_warp = gcap * (sizeof(CandSlot) + sizeof(HitRec) / 2 + 2);
+    const uint64_t max_table_warps = kNoAllocTableBytes / per_warp;
+    const bool tables = gcap > (uint64_t)scap;  // some read may outgrow shared memory
+    if (tables && max_table_warps < 1) {
+        set_error("%s: seeds x max_hits per read (%llu) needs %llu bytes of candidate "
+                  "table for one warp, more than the %llu this entry point holds (fewer seeds "
+                  "or a smaller max_hits, or use snap_align_device)",
+                  where, (unsigned long long)hs.max_hits_bound, (unsigned long long)per_warp,
+                  (unsigned long long)kNoAllocTableBytes);
+        return SNAP_E_INVAL;
     }
-    kfn<<<(unsigned)blocks, warps * 32, (size_t)warps * a.warp_words * 4, stream>>>(a);
+    const int aligned = ((reinterpret_cast<uintptr_t>(d_reads) + base0) % 16) == 0;
+    k_pack_reads<<<grid_cap(sms, nwords, 256), 256, 0, stream>>>(
+        d_reads, base0, hs.total_bases, d_words, nwords, aligned, &d_st->status);
+    SNAP_CUDA(cudaGetLastError(), "pack launch");
+
+    // first launch: every SM full of warps, shared-memory tables only; a read whose
+    // candidates outgrow them is listed for the second launch
+    const uint64_t blocks1 = std::min<uint64_t>((uint64_t)sms * per_sm, (n + warps - 1) / warps);
+    if (tables) {
+        a.defer_ids = d_defer;
+        a.defer_count = d_q + 2;
+        a.defer_cap = kNoAllocDeferIds;
+    }
+    kfn<<<(unsigned)std::max<uint64_t>(1, blocks1), warps * 32, smem, stream>>>(a);
     SNAP_CUDA(cudaGetLastError(), "align launch");
     int st = 0;
+    unsigned long long ndefer = 0;
+    SNAP_CUDA(cudaMemcpyAsync(&st, &d_st->status, sizeof(int), cudaMemcpyDeviceToHost, stream),
+              "status");
+    SNAP_CUDA(cudaMemcpyAsync(&ndefer, d_q + 2, sizeof(ndefer), cudaMemcpyDeviceToHost, stream),
+              "listed reads");
+    SNAP_CUDA(cudaStreamSynchronize(stream), where);
+    if (st & kStTableFull) {
+        set_error("%s: more than %llu reads of the batch need a candidate table larger than "
+                  "shared memory (split the batch or use snap_align_device)",
+                  where, (unsigned long long)kNoAllocDeferIds);
+        return SNAP_E_INVAL;
+    }
+    if (st || ndefer == 0) return status_to_code(st, where);
+
+    // second launch: the listed reads, as many warps as the array has tables for
+    int warps2 = (int)std::min<uint64_t>((uint64_t)warps, max_table_warps);
+    const uint64_t tw_cap = std::min<uint64_t>(max_table_warps, (uint64_t)sms * per_sm * warps2);
+    uint64_t blocks2 = std::min<uint64_t>(tw_cap / warps2, (ndefer + warps2 - 1) / warps2);
+    blocks2 = std::max<uint64_t>(1, blocks2);
+    const uint64_t tw = blocks2 * warps2;
+    a.defer_ids = nullptr;
+    a.defer_count = nullptr;
+    a.defer_cap = 0;
+    a.order = d_defer;
+    a.n_items = ndefer;
+    a.head = d_q + 1;
+    a.gtab = reinterpret_cast<CandSlot*>(d_tables);
+    a.ghits = reinterpret_cast<HitRec*>(d_tables + tw * gcap * sizeof(CandSlot));
+    a.gdense = reinterpret_cast<uint32_t*>(d_tables + tw * gcap * sizeof(CandSlot) +
+                                           tw * (gcap / 2) * sizeof(HitRec));
+    a.gcap = (uint32_t)gcap;
+    // the array keeps the previous call's contents: empty the tables this launch uses
+    k_init_ctab<<<grid_cap(sms, tw * gcap, 256), 256, 0, stream>>>(a.gtab, tw * gcap);
+    SNAP_CUDA(cudaGetLastError(), "table init");
+    kfn<<<(unsigned)blocks2, warps2 * 32, (size_t)warps2 * a.warp_words * 4, stream>>>(a);
+    SNAP_CUDA(cudaGetLastError(), "align launch");
     SNAP_CUDA(cudaMemcpyAsync(&st, &d_st->status, sizeof(int), cudaMemcpyDeviceToHost, stream),
               "status");
     SNAP_CUDA(cudaStreamSynchronize(stream), where);
