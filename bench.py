@@ -60,6 +60,8 @@ def _args():
                     help="serving run (C4 recipe): Poisson arrivals at --load x the measured "
                          "capacity, p50/p99 request latency")
     ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the bounded serving pass in the default run (0: none)")
     ap.add_argument("--load", type=float, default=0.7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -90,6 +92,7 @@ def _args():
     if args.profile:
         args.no_plain = args.no_cpu_baseline = True
         args.e2e_steps = 0
+        args.serve_requests = 0
         args.calls_per_step = args.calls_per_step or 1
     return args
 
@@ -634,6 +637,18 @@ def run_ours(args):
                                                  (0 if dpr is None else dpr.nbytes)),
                        "d2h_bytes_per_step": int(16 * n), "steps": args.e2e_steps}
 
+    # a bounded serving pass: C4-recipe requests (100-1,000 reads each, 80% 100 bp and
+    # 20% 1-10 kb at 5% error) on this workload's genome, p50/p99 latency at 0.7 x
+    # the measured capacity, and the plain form on the same request stream
+    if rank == 0 and args.serve_requests > 0 and not plain:
+        import synth
+        reqs = make_requests(g, synth.CONFIGS["C4"], args.serve_requests, 100, 1000,
+                             first=10_000_000)
+        sv = serving_pass(snap, idx, reqs, synth.CONFIGS["C4"].params(), args.load)
+        sv["workload"] = (f"C4 recipe requests (log-uniform 100-1000 reads; 80% 100 bp, 20% "
+                          f"1-10 kb at 5% error) on the {w.G // 1_000_000} Mbp genome")
+        line["serving"] = sv
+
     if rank == 0 and not args.no_cpu_baseline:
         cb, sample, ref = cpu_oracle_sample(w, g, rd, dpr, stride=args.stride)
         line["cpu_baseline"] = cb
@@ -648,10 +663,99 @@ def run_ours(args):
     return 0
 
 
+def make_requests(g, w, n_requests: int, lo: int, hi: int, first: int = 0):
+    """Serving requests of the C4 recipe on genome g: request sizes log-uniform in
+    [lo, hi] reads, each read 100 bp (80%) or log-uniform 1-10 kb (20%), 5% error,
+    d_max = max(8, ceil(0.08 m)).  Returns [(reads, d_max per read)]."""
+    import synth
+    _, sizes = synth.arrivals(n_requests, 1.0, lo, hi)
+    reqs = []
+    for k, nr in enumerate(sizes.tolist()):
+        lens = synth.read_lengths(nr, 2, 100, 1000, 10000, 0.8, seed=1000 + k)
+        rd = synth.reads(g, lens, w.sub_rate, w.indel_rate, w.indel_len, first_index=first)
+        first += nr
+        reqs.append((rd, w.max_dist_per_read(rd.lengths())))
+    return reqs
+
+
+def serving_pass(snap, gi, reqs, params, load: float, max_inflight: int = 4,
+                 plain_compare: bool = True, mem_budget_bytes: int = 64 << 30):
+    """Serve `reqs` on index gi: first all at once (capacity), then submitted at
+    Poisson arrival times at load x capacity; latency = completion - submission.
+    With plain_compare, the same requests also go one at a time through the plain
+    one-launch-per-stage form at the same arrival times (a request waits for the one
+    before it).  Returns a dict of reads/s, capacity and p50/p99 latency."""
+    import synth
+    total_reads = int(sum(r.n for r, _ in reqs))
+    total_bases = int(sum(int(r.offsets[-1]) for r, _ in reqs))
+    srv = snap.Server(gi, mem_budget_bytes=mem_budget_bytes, max_inflight=max_inflight)
+    try:
+        for rd, dpr in reqs[:3]:  # warm-up (tuning, graphs)
+            srv.wait(srv.submit(rd.bases, rd.offsets, max_dist_per_read=dpr, **params))
+        t0 = time.perf_counter()
+        tk = [srv.submit(rd.bases, rd.offsets, max_dist_per_read=dpr, **params)
+              for rd, dpr in reqs]
+        results = [srv.wait(t)[0] for t in tk]
+        cap_s = time.perf_counter() - t0
+        capacity = total_reads / cap_s
+        rate = load * capacity / (total_reads / len(reqs))  # requests per second
+        times, _ = synth.arrivals(len(reqs), rate, 1, 2)
+        lat = [0.0] * len(reqs)
+        tickets = [None] * len(reqs)
+        start = time.perf_counter()
+        for k, (rd, dpr) in enumerate(reqs):
+            delay = start + float(times[k]) - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = srv.submit(rd.bases, rd.offsets, max_dist_per_read=dpr, **params)
+        same = True
+        for k in range(len(reqs)):
+            res, lat[k] = srv.wait(tickets[k])
+            same &= all(np.array_equal(res[f], results[k][f])
+                        for f in ("location", "edit_distance", "strand", "cls"))
+        wall = time.perf_counter() - start
+    finally:
+        srv.close()
+    out = {"requests": len(reqs), "reads": total_reads, "bases": total_bases,
+           "max_inflight": max_inflight, "offered_load": load, "arrival_rate_per_s": rate,
+           "capacity_reads_per_s": capacity, "capacity_bases_per_s": total_bases / cap_s,
+           "value_reads_per_s": total_reads / wall,
+           "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+           "max_s": float(max(lat)), "results_same_alone_and_in_mix": bool(same)}
+    if plain_compare:
+        # the plain form on the same requests: capacity back to back, then the same
+        # arrival times with one request on the device at a time
+        for rd, dpr in reqs[:2]:
+            gi.align(rd.bases, rd.offsets, max_dist_per_read=dpr, plain=True, **params)
+        t0 = time.perf_counter()
+        same_plain = True
+        for k, (rd, dpr) in enumerate(reqs):
+            res = gi.align(rd.bases, rd.offsets, max_dist_per_read=dpr, plain=True, **params)
+            same_plain &= all(np.array_equal(res[f], results[k][f])
+                              for f in ("location", "edit_distance", "strand", "cls"))
+        p_cap = total_reads / (time.perf_counter() - t0)
+        plat = []
+        start = time.perf_counter()
+        for k, (rd, dpr) in enumerate(reqs):
+            arrive = start + float(times[k])
+            delay = arrive - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            gi.align(rd.bases, rd.offsets, max_dist_per_read=dpr, plain=True, **params)
+            plat.append(time.perf_counter() - arrive)
+        p_wall = time.perf_counter() - start
+        out["plain"] = {"capacity_reads_per_s": p_cap, "value_reads_per_s": total_reads / p_wall,
+                        "p50_s": float(np.percentile(plat, 50)),
+                        "p99_s": float(np.percentile(plat, 99)),
+                        "identical_results": bool(same_plain)}
+        out["served_over_plain_capacity"] = capacity / p_cap
+    return out
+
+
 def run_serve(args):
-    """C4 serving run: requests of log-uniform size (1k-100k reads; 80% 100 bp, 20%
-    1-10 kb), first all submitted at once to measure capacity, then submitted at
-    Poisson arrival times at --load x capacity; latency = completion - arrival."""
+    """C4 serving run on the 3.1 Gbp genome: requests of log-uniform size (1k-100k
+    reads; 80% 100 bp, 20% 1-10 kb), first all submitted at once to measure
+    capacity, then submitted at Poisson arrival times at --load x capacity."""
     import torch
 
     import paper_1111_5572_gb300 as snap
@@ -667,54 +771,21 @@ def run_serve(args):
     t0 = time.perf_counter()
     gi = snap.Index(g, w.seed_len)
     build_s = time.perf_counter() - t0
-    _, sizes = synth.arrivals(args.requests, 1.0, 1000, 100_000)
-    reqs, first = [], 0
-    for k, nr in enumerate(sizes.tolist()):
-        lens = synth.read_lengths(nr, 2, 100, 1000, 10000, 0.8, seed=1000 + k)
-        rd = synth.reads(g, lens, w.sub_rate, w.indel_rate, w.indel_len, first_index=first)
-        first += nr
-        reqs.append((rd, w.max_dist_per_read(rd.lengths())))
-    total_reads = int(sum(r.n for r, _ in reqs))
-    total_bases = int(sum(int(r.offsets[-1]) for r, _ in reqs))
-    srv = snap.Server(gi, mem_budget_bytes=64 << 30, max_inflight=4)
-    # warm-up (tuning, graphs) on the first requests
-    for rd, dpr in reqs[:3]:
-        srv.wait(srv.submit(rd.bases, rd.offsets, max_dist_per_read=dpr, **w.params()))
-    # capacity: everything submitted at once
-    t0 = time.perf_counter()
-    tk = [srv.submit(rd.bases, rd.offsets, max_dist_per_read=dpr, **w.params())
-          for rd, dpr in reqs]
-    for t in tk:
-        srv.wait(t)
-    cap_s = time.perf_counter() - t0
-    capacity = total_reads / cap_s
-    # open loop: Poisson arrivals at load x capacity (requests/s)
-    rate = args.load * capacity / (total_reads / len(reqs))
-    times, _ = synth.arrivals(args.requests, rate, 1000, 100_000)
-    lat = [0.0] * len(reqs)
-    tickets = [None] * len(reqs)
+    reqs = make_requests(g, w, args.requests, 1000, 100_000)
     with ClockSampler(0) as clk:
-        start = time.perf_counter()
-        for k, (rd, dpr) in enumerate(reqs):
-            delay = start + float(times[k]) - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            tickets[k] = srv.submit(rd.bases, rd.offsets, max_dist_per_read=dpr, **w.params())
-        for k in range(len(reqs)):
-            _, lat[k] = srv.wait(tickets[k])
-        wall = time.perf_counter() - start
-    srv.close()
+        sv = serving_pass(snap, gi, reqs, w.params(), args.load, plain_compare=False)
     line = {
-        "metric": METRIC, "mode": "serve", "value": total_reads / wall, "unit": "reads/s",
+        "metric": METRIC, "mode": "serve", "value": sv["value_reads_per_s"], "unit": "reads/s",
         "n_gpus": 1, "higher_is_better": True, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": w.name, "genome_bp": w.G, "requests": len(reqs),
-                   "reads": total_reads, "bases": total_bases, "max_inflight": 4,
-                   "offered_load": args.load, "arrival_rate_per_s": rate},
-        "capacity_reads_per_s": capacity, "capacity_bases_per_s": total_bases / cap_s,
-        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                      "max": float(max(lat))},
-        "bases_per_s": total_bases / wall, "index_build_s": build_s, "genome_gen_s": gen_s,
-        "clocks": clk.summary(),
+        "config": {"workload": w.name, "genome_bp": w.G, "request_reads": "log-uniform "
+                   "[1000, 100000]", **{k: sv[k] for k in ("requests", "reads", "bases",
+                                                          "max_inflight", "offered_load",
+                                                          "arrival_rate_per_s")}},
+        "capacity_reads_per_s": sv["capacity_reads_per_s"],
+        "capacity_bases_per_s": sv["capacity_bases_per_s"],
+        "latency_s": {"p50": sv["p50_s"], "p99": sv["p99_s"], "max": sv["max_s"]},
+        "results_same_alone_and_in_mix": sv["results_same_alone_and_in_mix"],
+        "index_build_s": build_s, "genome_gen_s": gen_s, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
     return 0
