@@ -84,6 +84,11 @@ def _args():
     ap.add_argument("--sweep-gather", action="store_true",
                     help="the random-gather ceiling over chunk sizes, chunks in flight per "
                          "thread and threads per SM (one JSON line)")
+    ap.add_argument("--collapse", action="store_true",
+                    help="exact-duplicate collapsing in the parallel drain "
+                         "(snap_params.collapse_duplicates = 1)")
+    ap.add_argument("--divergence", type=float, default=None,
+                    help="divergence of repeat copies (default: the recipe's 2%%)")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up plus the timed steps only (no plain form, e2e or CPU "
                          "baseline): the command to run under ncu")
@@ -294,7 +299,11 @@ def make_workload(args, rank: int):
     if args.genome_bp:
         w = w.scaled(G=args.genome_bp, n_reads=n)
     t0 = time.perf_counter()
-    g, _ = w.make_genome()
+    if args.divergence is None:
+        g, _ = w.make_genome()
+    else:
+        g, _ = synth.genome(w.G, w.repeat_frac, divergence=args.divergence)
+        w = w.scaled(G=w.G, n_reads=n, name=f"{w.name}-divergence-{args.divergence:g}")
     rd = w.make_reads(g, n=n, first_index=rank * n)
     dpr = w.max_dist_per_read(rd.lengths())
     return w, g, rd, dpr, time.perf_counter() - t0
@@ -404,6 +413,8 @@ def run_ours(args):
     build_s = time.perf_counter() - t0
     info = idx.info()
     params = w.params()
+    if args.collapse:
+        params["collapse_duplicates"] = 1
     plain = args.form == "plain"
 
     d_b = torch.from_numpy(rd.bases).to(dev)
@@ -539,7 +550,7 @@ def run_ours(args):
                                "frac": span_bytes / (span_ms / 1e3) / 1e9 / peak},
                 "counters": {k: tot(k) for k in ("reads", "seeds", "slot_reads", "list_entries",
                                                  "ed_calls", "ed_over", "window_bytes",
-                                                 "ed_filtered", "reads_light", "light_seeds",
+                                                 "ed_filtered", "ed_collapsed", "reads_light", "light_seeds",
                                                  "light_list_entries", "light_ed_calls")}}
     # the practical ceiling of this traffic: independent random reads of one
     # aligned chunk (a 64-byte index bucket, a 32-byte sector); not under

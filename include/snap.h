@@ -69,6 +69,14 @@ typedef struct snap_server snap_server; /* opaque serving-loop state */
  *              the first k non-popular seeds (all of them when a read has fewer)
  *              vote before the first candidate is scored, then one candidate
  *              per seed as in Algorithm 1.
+ *   collapse_duplicates  0 (default) or 1: exact-duplicate collapsing, the
+ *              memoisation the paper lists as ongoing work (Ongoing Work,
+ *              Approach): when the candidates a warp scores together after the
+ *              Baeza-Yates test (the parallel drain of the warp-per-read kernel)
+ *              include genome windows that are identical base for base on the
+ *              same strand, the distance is computed once per distinct window and
+ *              shared.  Results never change; snap_call_stats.ed_collapsed counts
+ *              the distances it saved.  Other kernels ignore it.
  */
 typedef struct {
     int32_t max_dist;
@@ -77,6 +85,7 @@ typedef struct {
     int32_t num_seeds;
     const int32_t* max_dist_per_read;
     int32_t first_seeds;
+    int32_t collapse_duplicates;
 } snap_params;
 
 /*
@@ -292,6 +301,8 @@ typedef struct {
     uint64_t light_list_entries;
     uint64_t light_ed_calls;
     uint64_t light_window_bytes;
+    uint64_t ed_collapsed;        /* distances taken from an identical window on the same
+                                     strand (collapse_duplicates); counted in ed_calls */
 } snap_call_stats;
 
 int snap_last_call_stats(const snap_index* index, snap_call_stats* out);

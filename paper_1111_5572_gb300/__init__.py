@@ -41,7 +41,8 @@ class SnapError(RuntimeError):
 class snap_params(ctypes.Structure):
     _fields_ = [("max_dist", ctypes.c_int32), ("max_hits", ctypes.c_int32),
                 ("conf_diff", ctypes.c_int32), ("num_seeds", ctypes.c_int32),
-                ("max_dist_per_read", ctypes.c_void_p), ("first_seeds", ctypes.c_int32)]
+                ("max_dist_per_read", ctypes.c_void_p), ("first_seeds", ctypes.c_int32),
+                ("collapse_duplicates", ctypes.c_int32)]
 
 
 class snap_index_info(ctypes.Structure):
@@ -66,7 +67,7 @@ class snap_call_stats(ctypes.Structure):
                 ("light_ms", ctypes.c_double), ("reads_light", ctypes.c_uint64),
                 ("light_seeds", ctypes.c_uint64), ("light_slot_reads", ctypes.c_uint64),
                 ("light_list_entries", ctypes.c_uint64), ("light_ed_calls", ctypes.c_uint64),
-                ("light_window_bytes", ctypes.c_uint64)]
+                ("light_window_bytes", ctypes.c_uint64), ("ed_collapsed", ctypes.c_uint64)]
 
 
 _lib = None
@@ -121,9 +122,10 @@ def _p(a: Optional[np.ndarray]):
 
 
 def make_params(max_dist: int = 8, max_hits: int = 300, conf_diff: int = 2, num_seeds: int = 0,
-                max_dist_per_read_ptr: Optional[int] = None, first_seeds: int = 0) -> snap_params:
+                max_dist_per_read_ptr: Optional[int] = None, first_seeds: int = 0,
+                collapse_duplicates: int = 0) -> snap_params:
     return snap_params(int(max_dist), int(max_hits), int(conf_diff), int(num_seeds),
-                       max_dist_per_read_ptr, int(first_seeds))
+                       max_dist_per_read_ptr, int(first_seeds), int(collapse_duplicates))
 
 
 def measure_gather(buffer_bytes: int = 8 << 30, chunk_bytes: int = 32,
@@ -191,7 +193,8 @@ class Index:
     def align(self, bases: np.ndarray, offsets: np.ndarray, max_dist: int = 8,
               max_hits: int = 300, conf_diff: int = 2, num_seeds: int = 0,
               max_dist_per_read: Optional[np.ndarray] = None, plain: bool = False,
-              out: Optional[np.ndarray] = None, first_seeds: int = 0) -> np.ndarray:
+              out: Optional[np.ndarray] = None, first_seeds: int = 0,
+              collapse_duplicates: int = 0) -> np.ndarray:
         """Host buffers in, host results out (snap_align / snap_align_plain)."""
         bases = np.ascontiguousarray(bases, dtype=np.uint8)
         offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
@@ -201,7 +204,8 @@ class Index:
         dpr = None if max_dist_per_read is None else np.ascontiguousarray(max_dist_per_read,
                                                                           dtype=np.int32)
         prm = make_params(max_dist, max_hits, conf_diff, num_seeds,
-                          None if dpr is None else dpr.ctypes.data, first_seeds)
+                          None if dpr is None else dpr.ctypes.data, first_seeds,
+                          collapse_duplicates)
         fn = load_library().snap_align_plain if plain else load_library().snap_align
         _check(fn(self._h, _p(bases), _p(offsets), n, ctypes.byref(prm), _p(out)),
                "snap_align_plain" if plain else "snap_align")
@@ -209,12 +213,13 @@ class Index:
 
     def align_device(self, d_bases, d_offsets, d_out, max_dist: int = 8, max_hits: int = 300,
                      conf_diff: int = 2, num_seeds: int = 0, d_max_dist_per_read=None,
-                     stream=None, plain: bool = False, first_seeds: int = 0):
+                     stream=None, plain: bool = False, first_seeds: int = 0,
+                     collapse_duplicates: int = 0):
         """Device tensors (torch, uint8 / int64 / 16-byte rows) on `stream` (torch.cuda.Stream)."""
         n = int(d_offsets.numel() - 1)
         prm = make_params(max_dist, max_hits, conf_diff, num_seeds,
                           None if d_max_dist_per_read is None else d_max_dist_per_read.data_ptr(),
-                          first_seeds)
+                          first_seeds, collapse_duplicates)
         st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
         fn = (load_library().snap_align_plain_device if plain
               else load_library().snap_align_device)
@@ -226,13 +231,14 @@ class Index:
 
     def align_device_noalloc(self, d_bases, d_offsets, d_out, max_dist: int = 8,
                              max_hits: int = 300, conf_diff: int = 2, num_seeds: int = 0,
-                             d_max_dist_per_read=None, stream=None, first_seeds: int = 0):
+                             d_max_dist_per_read=None, stream=None, first_seeds: int = 0,
+                             collapse_duplicates: int = 0):
         """snap_align_device_noalloc: the library allocates no device memory for this call
         (for callers that must not see cudaMalloc/cudaFree); limits in include/snap.h."""
         n = int(d_offsets.numel() - 1)
         prm = make_params(max_dist, max_hits, conf_diff, num_seeds,
                           None if d_max_dist_per_read is None else d_max_dist_per_read.data_ptr(),
-                          first_seeds)
+                          first_seeds, collapse_duplicates)
         st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
         _check(load_library().snap_align_device_noalloc(
             self._h, ctypes.c_void_p(d_bases.data_ptr()), ctypes.c_void_p(d_offsets.data_ptr()),
@@ -265,13 +271,15 @@ class Server:
 
     def submit(self, bases: np.ndarray, offsets: np.ndarray, max_dist: int = 8,
                max_hits: int = 300, conf_diff: int = 2, num_seeds: int = 0,
-               max_dist_per_read: Optional[np.ndarray] = None, first_seeds: int = 0) -> int:
+               max_dist_per_read: Optional[np.ndarray] = None, first_seeds: int = 0,
+               collapse_duplicates: int = 0) -> int:
         bases = np.ascontiguousarray(bases, dtype=np.uint8)
         offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
         dpr = None if max_dist_per_read is None else np.ascontiguousarray(max_dist_per_read,
                                                                           dtype=np.int32)
         prm = make_params(max_dist, max_hits, conf_diff, num_seeds,
-                          None if dpr is None else dpr.ctypes.data, first_seeds)
+                          None if dpr is None else dpr.ctypes.data, first_seeds,
+                          collapse_duplicates)
         t = ctypes.c_uint64()
         _check(load_library().snap_server_submit(self._h, _p(bases), _p(offsets),
                                                  int(offsets.shape[0] - 1), ctypes.byref(prm),

@@ -351,6 +351,7 @@ struct FusedArgs {
     unsigned long long* head;
     int d_max, h_max, c, num_seeds;
     int first_seeds;  // non-popular seeds that vote before the first pick (<= 1: Algorithm 1)
+    int collapse;     // share distances between identical windows in the parallel drain
     int stride;       // index stride: probes per seed
     const int32_t* dmax_per_read;
     uint8_t shifts[32];
@@ -384,21 +385,21 @@ struct FusedArgs {
 struct WarpCounters {
     uint32_t seeds = 0, slot_reads = 0, list_entries = 0, ed_calls = 0, ed_over = 0;
     unsigned long long window_words = 0;
-    uint32_t ed_filtered = 0, reads_done = 0;
+    uint32_t ed_filtered = 0, reads_done = 0, ed_collapsed = 0;
 };
 
 __device__ __forceinline__ void flush_counters(DevCounters* ctr, WarpCounters& c) {
-    unsigned long long v[8] = {c.seeds, c.slot_reads, c.list_entries, c.ed_calls, c.ed_over,
-                               c.window_words, c.ed_filtered, c.reads_done};
+    unsigned long long v[9] = {c.seeds, c.slot_reads, c.list_entries, c.ed_calls, c.ed_over,
+                               c.window_words, c.ed_filtered, c.reads_done, c.ed_collapsed};
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 9; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
     }
     if ((threadIdx.x & 31) == 0) {
         unsigned long long* dst = &ctr->seeds;
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < 9; ++k)
             if (v[k]) atomicAdd(dst + k, v[k]);
     }
 }
@@ -952,6 +953,8 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                     int d0 = kOver;
                     unsigned words = 0;
                     unsigned long long my_key = 0;
+                    bool staged = false;  // this lane's window is in Tp
+                    int my_tb = 0, my_n = 0;
                     if (lane < k) {
                         my_key = tab[chunk[lane]].key;
                         if (Lc >= 0) {
@@ -963,11 +966,55 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                                 const uint32_t* gw = a.genome + (p >> 4);
                                 for (int w = 0; w < nwt; ++w) Tp[w * 32 + lane] = __ldg(gw + w);
                                 words = (unsigned)nwt;
-                                d0 = lv_lane((my_key & 1) ? wm.Xr : wm.Xf, 1, m, Tp + lane, 32, tb,
-                                             n_t, Lc, Rp + lane, 32);
+                                staged = true;
+                                my_tb = tb;
+                                my_n = n_t;
                             } else {
                                 atomicOr(a.status, kStInternal);  // cannot happen: layout bug
                             }
+                        }
+                    }
+                    // exact-duplicate collapsing: a lane whose window equals, base for
+                    // base and on the same strand, that of a lower lane of the chunk
+                    // takes that lane's distance instead of computing its own
+                    int leader = lane;
+                    if (a.collapse) {
+                        __syncwarp();
+                        uint64_t h = 0;
+                        if (staged) {
+                            h = mix64((uint64_t)my_n * 2 + (my_key & 1));
+                            for (int b = 0; b < my_n; b += 16) {
+                                uint32_t x = get16s(Tp + lane, my_tb + b, 32);
+                                if (my_n - b < 16) x &= (1u << (2 * (my_n - b))) - 1u;
+                                h = mix64(h ^ x);
+                            }
+                        }
+                        const int my_sn = staged ? 2 * my_n + (int)(my_key & 1) + 1 : 0;
+                        for (int q = 0; q < 32; ++q) {
+                            const uint64_t hq = __shfl_sync(kFull, h, q);
+                            const int snq = __shfl_sync(kFull, my_sn, q);  // length, strand
+                            const int tq = __shfl_sync(kFull, my_tb, q);
+                            if (staged && leader == lane && q < lane && snq == my_sn && hq == h) {
+                                // same hash: compare the two windows exactly
+                                bool same = true;
+                                for (int b = 0; b < my_n && same; b += 16) {
+                                    uint32_t x = get16s(Tp + lane, my_tb + b, 32) ^
+                                                 get16s(Tp + q, tq + b, 32);
+                                    if (my_n - b < 16) x &= (1u << (2 * (my_n - b))) - 1u;
+                                    same = x == 0;
+                                }
+                                if (same) leader = q;
+                            }
+                        }
+                    }
+                    if (staged && leader == lane)
+                        d0 = lv_lane((my_key & 1) ? wm.Xr : wm.Xf, 1, m, Tp + lane, 32, my_tb,
+                                     my_n, Lc, Rp + lane, 32);
+                    if (a.collapse) {
+                        const int dl = __shfl_sync(kFull, d0, leader);
+                        if (leader != lane) {
+                            d0 = dl;
+                            wc.ed_collapsed++;
                         }
                     }
 #pragma unroll
@@ -1353,6 +1400,10 @@ int validate_params(const snap_index* idx, const snap_params* p) {
         set_error("max_hits %d outside [0, %u]", p->max_hits, kListMax);
         return SNAP_E_INVAL;
     }
+    if (p->collapse_duplicates != 0 && p->collapse_duplicates != 1) {
+        set_error("collapse_duplicates %d is neither 0 nor 1", p->collapse_duplicates);
+        return SNAP_E_INVAL;
+    }
     if (p->first_seeds < 0 || p->first_seeds > kMaxSeeds) {
         set_error("first_seeds %d outside [0, %d]", p->first_seeds, kMaxSeeds);
         return SNAP_E_INVAL;
@@ -1474,6 +1525,7 @@ static int finish_status(Engine* e, cudaStream_t stream, const char* where, uint
     L.ed_over = h->ctr.ed_over;
     L.window_bytes = h->ctr.window_words * 4;
     L.ed_filtered = h->ctr.ed_filtered;
+    L.ed_collapsed = h->ctr.ed_collapsed;
     L.light_threads = e->last_shape.light_threads;
     L.warps_per_block = e->last_shape.warps;
     L.table_slots = e->last_shape.scap;
@@ -1542,6 +1594,7 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     a.c = p->conf_diff;
     a.num_seeds = p->num_seeds;
     a.first_seeds = p->first_seeds;
+    a.collapse = p->collapse_duplicates;
     a.stride = idx->stride;
     a.dmax_per_read = p->max_dist_per_read;
     shift_list(idx->s, a.shifts, &a.n_shifts);
@@ -2151,6 +2204,7 @@ static int align_noalloc(const snap_index* idx, const uint8_t* d_reads, const ui
     a.c = p->conf_diff;
     a.num_seeds = p->num_seeds;
     a.first_seeds = p->first_seeds;
+    a.collapse = p->collapse_duplicates;
     a.stride = idx->stride;
     a.dmax_per_read = p->max_dist_per_read;
     shift_list(idx->s, a.shifts, &a.n_shifts);

@@ -88,7 +88,7 @@ struct HitRec {
 // Traffic counters accumulated by the align kernels (one atomicAdd per warp).
 struct DevCounters {
     unsigned long long seeds, slot_reads, list_entries, ed_calls, ed_over, window_words,
-        ed_filtered, reads_done;
+        ed_filtered, reads_done, ed_collapsed;
 };
 
 // Statistics of a read batch, computed on the device before the main launch.

@@ -3,7 +3,7 @@
 //
 // A read is handled here when it is short (m <= 128), uses at most 6 seeds, has a
 // largest edit-distance limit d_max + c - 1 <= 15 and its non-popular seeds hit at
-// most 16 index positions; the thread then runs the whole per-read loop alone:
+// most 8 index positions; the thread then runs the whole per-read loop alone:
 // seed probes, votes in a small per-thread candidate list, the most-voted pick,
 // the limit schedule, a Landau-Vishkin edit distance over one diagonal at a time,
 // best / second best over 32-base buckets and the exits.  An edit distance that
@@ -28,7 +28,11 @@ namespace snapgpu {
 constexpr int kLightMaxM = kLightBucketMaxM;
 constexpr int kLightMaxSeeds = kLightBucketMaxSeeds;
 constexpr int kLightMaxL = kLightBucketMaxL;
-constexpr int kLightMaxCands = 16;
+// Index hits a read may have and stay here.  The per-thread candidate arrays live
+// in local memory, whose footprint competes with shared memory for L1: 8 measured
+// faster than 4, 6, 12, 16, 24 or 32 on both the 5%- and the 50%-repeat recipes
+// (the warp kernel takes the rest).
+constexpr int kLightMaxCands = 8;
 // A thread posts its distance to the warp rather than start edit distance round 4
 // (16 diagonals done): the rare long distances would otherwise hold the other 31
 // lanes of the warp idle.
@@ -90,7 +94,7 @@ __device__ __forceinline__ uint64_t col32(const uint32_t* col, int i, int st) {
 // one picks, which keeps the common case's registers free.
 //
 // A thread first does everything that touches memory: its read, its seed
-// probes, the candidates its non-popular seeds vote for (at most 16), and for
+// probes, the candidates its non-popular seeds vote for (at most 8), and for
 // each candidate an edit distance at the read's largest limit L0 = d_max + c - 1
 // stopped before a fifth round.  It then runs Algorithm 1 on those results: the
 // pick order depends only on the votes, and a distance at any limit L <= L0

@@ -79,6 +79,29 @@ def test_c5_repeat_dense_scaled(snap):
     assert st.n_multiple > 1000
 
 
+def test_exact_duplicate_collapsing(snap):
+    """Exact-duplicate collapsing (Ongoing Work, Approach): on a genome whose repeat
+    copies are exact, the parallel drain finds candidates with identical windows and
+    computes each distinct window's distance once; every result equals the run without
+    collapsing and the oracle's."""
+    G = 5_000_000
+    g, _ = synth.genome(G, 0.3, divergence=0.0)
+    w = synth.CONFIGS["C5"].scaled(G=G, n_reads=30_000)
+    rd = synth.reads(g, np.full(30_000, 100, dtype=np.uint32), w.sub_rate, w.indel_rate,
+                     w.indel_len, seed=31)
+    gi = snap.Index(g, w.seed_len)
+    off = gi.align(rd.bases, rd.offsets, **w.params())
+    assert gi.last_call_stats()["ed_collapsed"] == 0
+    on = gi.align(rd.bases, rd.offsets, collapse_duplicates=1, **w.params())
+    st = gi.last_call_stats()
+    assert st["ed_collapsed"] > 1000, st["ed_collapsed"]
+    assert_same(on, off, "collapsing on vs off")
+    ref, _ = oracle.Index(g, w.seed_len).align(rd.bases, rd.offsets, threads=16, **w.params())
+    assert_same(on, ref, "collapsing vs oracle")
+    with pytest.raises(snap.SnapError):
+        gi.align(rd.bases[:100], rd.offsets[:2], collapse_duplicates=2, **w.params())
+
+
 @pytest.mark.parametrize("h_max", [30, 3000])
 def test_hmax_sweep_points(snap, h_max):
     # the h_max sweep's end points on the repeat-dense recipe (seeds hitting 30-3000
