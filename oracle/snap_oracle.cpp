@@ -20,8 +20,7 @@
 //   * per-read loop: Algorithm 1 ("SNAP alignment algorithm"), with the
 //     32-base bucket merge of item 1 of the list after it.
 //
-// Readings taken where the paper is silent (each one is listed in the design
-// notes of the repository):
+// Readings taken where the paper is silent:
 //   R1 count(S) = occurrences of S + occurrences of revcomp(S).  A forward
 //      occurrence of S at l votes for (strand 0, p = l - o); an occurrence of
 //      revcomp(S) at l votes for (strand 1, p = l - (m - o - s)), where o is the
