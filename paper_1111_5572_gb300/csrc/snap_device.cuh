@@ -77,8 +77,13 @@ __device__ __forceinline__ IndexSlot load_slot(const IndexSlot* slots, uint64_t 
 // The index table is a sequence of 64-byte buckets of four slots (T is a
 // multiple of 4).  A key lives in its home bucket mulhi(mix(key), T/4) or, when
 // that bucket was full at insertion, in the next non-full bucket; slots of a
-// bucket fill in order, so an empty slot ends a lookup.
+// bucket fill in order, so an empty slot ends a lookup.  For seeds of at most 31
+// bases (keys below 2^62) the top bit of a bucket's first key says whether some
+// key whose home is this bucket spilled into a later one: a full home bucket
+// without that bit ends the lookup of a key it does not hold.
 constexpr int kBucketSlots = 4;
+constexpr unsigned long long kSpillBit = 1ull << 63;
+__host__ __device__ constexpr bool spill_flags(int s) { return s <= 31; }
 
 __device__ __forceinline__ uint64_t home_bucket(uint64_t key, uint64_t T) {
     return __umul64hi(mix64(key), T / kBucketSlots);
@@ -88,7 +93,8 @@ __device__ __forceinline__ uint64_t home_bucket(uint64_t key, uint64_t T) {
 // kStProbeRunaway in *status if the probe does not end within the table (a full
 // table; cannot happen at load <= 2/3).  *steps counts slots read.
 __device__ __forceinline__ bool probe_index(const IndexSlot* slots, uint64_t T, uint64_t K,
-                                            IndexSlot* out, int* status, uint32_t* steps) {
+                                            IndexSlot* out, int* status, uint32_t* steps,
+                                            bool flagged) {
     const uint64_t nb = T / kBucketSlots;
     uint64_t b = home_bucket(K, T);
     for (uint64_t step = 0; step < nb; ++step) {
@@ -98,9 +104,12 @@ __device__ __forceinline__ bool probe_index(const IndexSlot* slots, uint64_t T, 
         for (int j = 0; j < kBucketSlots; ++j) v[j] = __ldg(q + j);
         *steps += kBucketSlots;
         bool empty = false;
+        const unsigned long long first = ((unsigned long long)v[0].y << 32) | v[0].x;
 #pragma unroll
         for (int j = 0; j < kBucketSlots; ++j) {
-            const unsigned long long key = ((unsigned long long)v[j].y << 32) | v[j].x;
+            unsigned long long key = ((unsigned long long)v[j].y << 32) | v[j].x;
+            empty |= (key == kEmptyKey);
+            if (j == 0 && flagged) key &= ~kSpillBit;
             if (key == K) {
                 out->key = key;
                 out->field = v[j].z;
@@ -108,9 +117,9 @@ __device__ __forceinline__ bool probe_index(const IndexSlot* slots, uint64_t T, 
                 out->nB = (uint16_t)(v[j].w >> 16);
                 return true;
             }
-            empty |= (key == kEmptyKey);
         }
         if (empty) return false;
+        if (step == 0 && flagged && !(first & kSpillBit)) return false;  // none spilled
         b = (b + 1 == nb) ? 0 : b + 1;
     }
     atomicOr(status, kStProbeRunaway);
@@ -132,7 +141,7 @@ __device__ __forceinline__ void lookup_seed(const IndexSlot* slots, uint64_t T,
     rec->fwd_ref = rec->rc_ref = 0;
     rec->fwd_n = rec->rc_n = 0;
     *count = 0;
-    if (!probe_index(slots, T, K, &sl, status, steps)) return;
+    if (!probe_index(slots, T, K, &sl, status, steps, spill_flags(s))) return;
     const uint32_t nA = sl.nA, nB = sl.nB;
     // where A and B start: inline when nA + nB == 1
     const bool single = (nA + nB) == 1;

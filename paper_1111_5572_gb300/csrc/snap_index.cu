@@ -177,6 +177,20 @@ __global__ void k_fill(const uint32_t* __restrict__ words, uint64_t npos, int s,
     }
 }
 
+// After every key is placed: for each key that sits outside its home bucket, set
+// kSpillBit on the home bucket's first key (that bucket is full, so its first
+// slot holds a key; keys of s <= 31 bases never use the bit).
+__global__ void k_mark_spills(IndexSlot* slots, uint64_t T) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < T;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long key =
+            *reinterpret_cast<volatile unsigned long long*>(&slots[i].key);
+        if (key == kEmptyKey) continue;
+        const uint64_t h = home_bucket(key & ~kSpillBit, T);
+        if (h != i / kBucketSlots) atomicOr(&slots[h * kBucketSlots].key, kSpillBit);
+    }
+}
+
 static int grid_for(uint64_t n, int threads) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
@@ -314,6 +328,10 @@ extern "C" int snap_index_build_stride(const uint8_t* genome_ascii, uint64_t gen
                                                     which, d_status);
     }
     TRY(cudaGetLastError(), "fill launch");
+    if (spill_flags(seed_len)) {
+        k_mark_spills<<<grid_for(idx->T, 256), 256, 0, st>>>(idx->slots, idx->T);
+        TRY(cudaGetLastError(), "mark launch");
+    }
     TRY(cudaMemcpyAsync(&hstatus, d_status, sizeof(int), cudaMemcpyDeviceToHost, st), "status");
     TRY(cudaStreamSynchronize(st), "fill pass");
     if (hstatus) {
