@@ -275,7 +275,7 @@ typedef struct {
     uint64_t ed_calls;      /* edit distances computed */
     uint64_t ed_over;       /* of which over the limit */
     uint64_t window_bytes;  /* packed genome bytes staged for edit distances */
-    int32_t light_threads;    /* batched form: threads per block of the short-read bucket */
+    int32_t light_threads;    /* batched form: threads per block of the thread-per-read kernel */
     int32_t warps_per_block;  /* batched form: warps per block of the warp-per-read kernel */
     int32_t table_slots;      /* batched form: shared candidate slots per warp */
     int32_t graph_replay;     /* 1 when the launch sequence ran as a CUDA graph */
@@ -311,7 +311,7 @@ int snap_last_call_stats(const snap_index* index, snap_call_stats* out);
  * Options of the batched form on one index (both on by default):
  *   autotune     on the first batch of a new shape (read lengths, limits, seed
  *                count, batch size within a factor of two), time a few launch
- *                shapes (threads per block of the short-read bucket, warps per
+ *                shapes (threads per block of the thread-per-read kernel, warps per
  *                block and shared candidate slots of the warp-per-read kernel) on
  *                that batch and keep the fastest for later batches of that shape.
  *                Results never depend on the shape.

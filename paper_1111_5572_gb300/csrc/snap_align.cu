@@ -239,7 +239,7 @@ __global__ void k_pack_reads(const uint8_t* __restrict__ reads, uint64_t base, u
     if (bad) atomicOr(status, kStBadBase);
 }
 
-// Distribute the reads the warp kernel must take (the short-read bucket's
+// Distribute the reads the warp kernel must take (the thread-per-read kernel's
 // leftovers, or all reads) into per-length-class lists (warp-aggregated atomics).
 struct ClassLists {
     uint32_t* list;                     // class q at list + off[q]
@@ -363,8 +363,8 @@ struct FusedArgs {
     uint32_t gcap;
     SeedRec* gseeds;  // per-warp seed records (seed_cap each) when not in shared memory
     uint32_t* gqbits; // per-warp q-gram bitmaps (2 x kQWords) for large limits, or NULL
-    const SeedRec* hseeds;   // probe records of reads handed over by the short-read
-    const uint8_t* hprobed;  // bucket (kLightBucketMaxSeeds per read), flagged per read
+    const SeedRec* hseeds;   // probe records of reads handed over by the thread-per-read
+    const uint8_t* hprobed;  // kernel (kLightBucketMaxSeeds per read), flagged per read
     // when set, a read whose candidate table fits in no table this launch has is
     // listed here (defer_cap entries at most) instead of aligned; a later launch
     // aligns the listed reads (the allocation-free entry point)
@@ -767,7 +767,7 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
         // ---- seeds and index probes, one lane per probe ----
         unsigned int H = 0;
         int last_np = -1;  // last probe after which a pick happens (seeds-first variant)
-        // a read the short-read bucket probed before handing it over: its records
+        // a read the thread-per-read kernel probed before handing it over: its records
         const bool reuse = a.hprobed != nullptr && a.hprobed[r] != 0;
         if (reuse) {
             for (int i = lane; i < n; i += 32) {
@@ -1549,7 +1549,7 @@ static int finish_status(Engine* e, cudaStream_t stream, const char* where, uint
     return SNAP_OK;
 }
 
-// The launch plan of the batched form for one shape: whether the short-read
+// The launch plan of the batched form for one shape: whether the thread-per-read
 // bucket runs, and one warp-kernel launch per non-empty read-length class, each
 // laid out for its class's longest read and largest limit.
 struct BatchPlan {
@@ -1814,7 +1814,7 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
                        const BatchPrep& bp) {
     int rc;
     // batches that share the classes present, the limits' register layout, the
-    // short-read bucket and the size within a factor of two share a tuned shape
+    // thread-per-read kernel and the size within a factor of two share a tuned shape
     TuneKey key;
     key.lvd = 0;
     for (int q = 0; q < kClasses; ++q)

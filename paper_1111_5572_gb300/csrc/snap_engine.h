@@ -35,7 +35,7 @@ struct Engine {
     DevBuf stats, head, packed, gtab, ghits, gdense, heavy;
     DevBuf gseeds[4];  // per-class per-warp seed records of long reads
     DevBuf gqbits[4];  // per-class per-warp q-gram bitmaps (large limits)
-    DevBuf hseeds;     // probe records of the reads the short-read bucket hands over
+    DevBuf hseeds;     // probe records of the reads the thread-per-read kernel hands over
     DevBuf hprobed;    // per read: 1 when hseeds holds its records
     bool gtab_ready = false;  // gtab holds only empty slots
     DevBuf h_reads, h_offsets, h_out, h_dmax;  // device copies for the host-buffer entry points
@@ -81,7 +81,7 @@ inline int grid_cap(int sms, uint64_t n, int threads) {
     return (int)want;
 }
 
-// thread-per-read bucket (snap_light.cu): limits of the reads it takes
+// thread-per-read kernel (snap_light.cu): limits of the reads it takes
 constexpr int kLightBucketMaxM = 128;
 constexpr int kLightBucketMaxSeeds = 6;
 constexpr int kLightBucketMaxL = 15;
