@@ -1550,7 +1550,7 @@ static int finish_status(Engine* e, cudaStream_t stream, const char* where, uint
 }
 
 // The launch plan of the batched form for one shape: whether the thread-per-read
-// bucket runs, and one warp-kernel launch per non-empty read-length class, each
+// kernel runs, and one warp-kernel launch per non-empty read-length class, each
 // laid out for its class's longest read and largest limit.
 struct BatchPlan {
     LaunchShape shape;
