@@ -279,8 +279,9 @@ typedef struct {
     int32_t warps_per_block;  /* batched form: warps per block of the warp-per-read kernel */
     int32_t table_slots;      /* batched form: shared candidate slots per warp */
     int32_t graph_replay;     /* 1 when the launch sequence ran as a CUDA graph */
-    int32_t team_classes;     /* read-length classes aligned in team mode (one read per
-                                 block, all warps of the block on each edit distance) */
+    int32_t team_classes;     /* read-length classes aligned one read per block: team
+                                 mode (all warps of the block on each edit distance) or
+                                 wave mode (each warp on its own candidate) */
     uint64_t ed_filtered;     /* edit distances (counted in ed_calls and ed_over) proven
                                  over the limit by the q-gram bound without the rounds */
     double probe_ms;          /* plain form: the seed-probe stage kernel alone (its
@@ -303,6 +304,8 @@ typedef struct {
     uint64_t light_window_bytes;
     uint64_t ed_collapsed;        /* distances taken from an identical window on the same
                                      strand (collapse_duplicates); counted in ed_calls */
+    int32_t wave_classes;         /* of team_classes, those aligned in wave mode */
+    int32_t wave_warps;           /* warps (candidates per wave) of the last such class */
 } snap_call_stats;
 
 int snap_last_call_stats(const snap_index* index, snap_call_stats* out);
@@ -322,10 +325,14 @@ int snap_last_call_stats(const snap_index* index, snap_call_stats* out);
  *                -1 (default) picks per batch, team mode when the class has fewer
  *                than max(8, longest read / 12) reads per SM, else one warp per
  *                read; 0 always one warp per read; 1 always team mode (one read
- *                per block of 8 warps, all of them on each edit distance).
- *                Results never depend on it.
+ *                per block of 8 warps, all of them on each edit distance); 2
+ *                always wave mode (one read per block; each warp computes one of
+ *                the read's next picks in Algorithm 1's order, at a bound on the
+ *                limits to come, and the block's first warp replays them in
+ *                order); it falls back to team mode when the index has a
+ *                stride or first_seeds > 1.  Results never depend on it.
  * Passing autotune = 0 also forgets tuned shapes.  Returns SNAP_E_INVAL for a
- * NULL index or team outside -1..1.
+ * NULL index or team outside -1..2.
  */
 int snap_index_configure(snap_index* index, int autotune, int cuda_graphs, int team);
 

@@ -67,7 +67,8 @@ class snap_call_stats(ctypes.Structure):
                 ("light_ms", ctypes.c_double), ("reads_light", ctypes.c_uint64),
                 ("light_seeds", ctypes.c_uint64), ("light_slot_reads", ctypes.c_uint64),
                 ("light_list_entries", ctypes.c_uint64), ("light_ed_calls", ctypes.c_uint64),
-                ("light_window_bytes", ctypes.c_uint64), ("ed_collapsed", ctypes.c_uint64)]
+                ("light_window_bytes", ctypes.c_uint64), ("ed_collapsed", ctypes.c_uint64),
+                ("wave_classes", ctypes.c_int32), ("wave_warps", ctypes.c_int32)]
 
 
 _lib = None
@@ -177,8 +178,9 @@ class Index:
         return {f: getattr(inf, f) for f, _ in snap_index_info._fields_}
 
     def configure(self, autotune: bool = True, cuda_graphs: bool = True, team: int = -1):
-        """snap_index_configure: autotuning of launch shapes, CUDA-graph replay and team
-        mode of long-read classes (-1 chosen per batch, 0 never, 1 always)."""
+        """snap_index_configure: autotuning of launch shapes, CUDA-graph replay and the
+        block-per-read modes of long-read classes (-1 chosen per batch, 0 never,
+        1 team mode, 2 wave mode)."""
         _check(load_library().snap_index_configure(self._h, int(autotune), int(cuda_graphs),
                                                    int(team)),
                "snap_index_configure")

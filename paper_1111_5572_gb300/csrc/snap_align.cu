@@ -365,6 +365,9 @@ struct FusedArgs {
     uint32_t* gqbits; // per-warp q-gram bitmaps (2 x kQWords) for large limits, or NULL
     const SeedRec* hseeds;   // probe records of reads handed over by the thread-per-read
     const uint8_t* hprobed;  // kernel (kLightBucketMaxSeeds per read), flagged per read
+    // per read: its distinct candidates over all seeds (k_read_cost), which bounds
+    // the table it needs, or kNoCount when not counted; NULL when not computed
+    const uint32_t* read_nd;
     // when set, a read whose candidate table fits in no table this launch has is
     // listed here (defer_cap entries at most) instead of aligned; a later launch
     // aligns the listed reads (the allocation-free entry point)
@@ -657,6 +660,95 @@ __device__ void team_helper(const FusedArgs& a, const WarpMem& wm) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Wave mode.  Team mode spreads one edit distance over the block, with a block
+// barrier per diagonal round; when a class's reads carry many large-limit
+// candidates the rounds are barrier- and latency-bound, and a read whose
+// candidates are all near the limit holds one block for the whole tail of the
+// launch.  Wave mode instead gives each warp of the block a candidate of its
+// own.  Picks depend only on the votes, so the lead warp runs Algorithm 1 ahead
+// of its scores: it adds seeds and picks (one pick per non-popular seed, as in
+// the seed loop, or one per step of the drain) until it holds W picks, one per
+// warp.  Every warp computes its pick's distance at Lb = min(d_best, dmax) + c - 1,
+// which bounds every limit Algorithm 1 can use before those scores (d_best only
+// falls; see the parallel drain), and the lead replays the steps in order, each
+// score at its own limit with ED(L) = (d0 <= L ? d0 : over), and the exit tests
+// after each seed.  When the Baeza-Yates test passes at a step before the last,
+// the steps after it are undone (their seeds' votes taken back, their picks
+// unscored again, candidates left without votes retired), so the drain starts
+// from the state Algorithm 1 reaches there; an early return needs no undo.
+// Results are those of scoring one candidate at a time.
+// ---------------------------------------------------------------------------
+constexpr int32_t kPending = -4;  // picked in the current wave, not yet replayed
+constexpr int32_t kRetired = -3;  // no votes left after an undo: not a candidate
+constexpr uint32_t kNoPick = 0xffffffffu;
+constexpr int kWaveMaxWarps = 8;
+// job words: op, picks, Lb, read length, then per pick its key (2 words) and result
+constexpr int kWaveKeys = 4;
+constexpr int kWaveRes = kWaveKeys + 2 * kWaveMaxWarps;
+constexpr int kWaveJobWords = kWaveRes + kWaveMaxWarps + 4;
+static_assert(kWaveJobWords % 4 == 0, "wave job words keep 16-byte alignment");
+
+// Slot of a key that is in the table (kNoPick if it is not: cannot happen).
+__device__ __forceinline__ uint32_t table_find(const CandSlot* tab, uint32_t mask,
+                                               unsigned long long key) {
+    uint32_t h = (uint32_t)mix64(key) & mask;
+    for (uint32_t step = 0; step <= mask; ++step) {
+        const unsigned long long k = tab[h].key;
+        if (k == key) return h;
+        if (k == kEmptyKey) break;
+        h = (h + 1) & mask;
+    }
+    return kNoPick;
+}
+
+// One wave entry's distance by one warp: window staged in this warp's Tw, the
+// q-gram bound (bits: the strand's map, built by the lead), then the rounds.
+__device__ int wave_distance(const FusedArgs& a, const uint32_t* X, int m, unsigned long long key,
+                             int L, uint32_t* Tw, int* lvA, int* lvB, const uint32_t* bits,
+                             int lane, WarpCounters& wc) {
+    const uint64_t p = key >> 1;
+    const int n_t = (int)min(a.G - p, (uint64_t)(m + L));
+    const uint64_t w0 = p >> 4;
+    const int tb = (int)(p & 15);
+    const int nwt = (tb + n_t + 15) / 16 + 2;
+    for (int w = lane; w < nwt; w += 32) Tw[w] = __ldg(a.genome + w0 + w);
+    __syncwarp();
+    if (lane == 0) wc.window_words += (unsigned)nwt;
+    if (bits && use_qfilter(m, L) &&
+        count_qhits(Tw, tb, n_t, bits, lane) < (m - kQ + 1) - L * kQ) {
+        if (lane == 0) wc.ed_filtered++;
+        return kOver;
+    }
+    return lv_warp(X, m, Tw, tb, n_t, L, lane, lvA, lvB, a.status);
+}
+
+// Warp `g` > 0 of a wave block: its window and diagonal buffers follow the
+// lead's layout; runs posted waves until the lead posts kJobExit.
+__device__ void wave_helper(const FusedArgs& a, const WarpMem& wm, uint32_t* smem, int g,
+                            WarpCounters& wc) {
+    const int lane = threadIdx.x & 31;
+    uint32_t* Tw = smem + a.warp_words + (size_t)(g - 1) * (a.wt + a.lv_ints);
+    int* lvA = reinterpret_cast<int*>(Tw + a.wt);
+    int* lvB = lvA + a.lv_ints / 2;
+    for (;;) {
+        __syncthreads();  // wave posted
+        if (wm.job[0] == kJobExit) return;
+        const int w = wm.job[1], Lb = wm.job[2], m = wm.job[3];
+        if (g < w) {
+            const unsigned long long key =
+                (unsigned long long)(uint32_t)wm.job[kWaveKeys + 2 * g] |
+                ((unsigned long long)(uint32_t)wm.job[kWaveKeys + 2 * g + 1] << 32);
+            const int strand = (int)(key & 1);
+            const uint32_t* bits = wm.qbits ? wm.qbits + strand * kQWords : nullptr;
+            const int d = wave_distance(a, strand ? wm.Xr : wm.Xf, m, key, Lb, Tw, lvA, lvB, bits,
+                                        lane, wc);
+            if (lane == 0) wm.job[kWaveRes + g] = d;
+        }
+        __syncthreads();  // results in
+    }
+}
+
 // Edit distance of candidate `key` at limit L (warp-wide, result uniform).  LVD
 // selects the diagonal layout: D diagonals per lane in registers (L <= 32D/2 - 1),
 // 0 for shared memory (any L), or -1 for shared memory behind the q-gram bound.
@@ -729,9 +821,11 @@ __device__ __forceinline__ int candidate_distance(const FusedArgs& a, const Warp
 // VARIANT: the index has a stride > 1 or first_seeds > 1 (probe slots grouped
 // per seed, picks deferred); without it a probe is a seed and every non-popular
 // one picks.
-template <int LVD, bool TEAM, bool VARIANT>
+// WAVE: the lead warp of a wave block (see wave_helper); with VARIANT false only.
+template <int LVD, bool TEAM, bool VARIANT, bool WAVE = false>
 __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem& wm, uint64_t r,
                                                int lane, WarpCounters& wc) {
+    static_assert(!(WAVE && (VARIANT || TEAM)), "wave mode: plain index, first_seeds <= 1");
     const uint64_t o0 = a.offsets[r], o1 = a.offsets[r + 1];
     const int m = (int)(o1 - o0);
     const uint64_t rb = o0 - a.base0 + kReadPadBases;
@@ -824,8 +918,11 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
             if (VARIANT) last_np = max(last_np, __shfl_xor_sync(kFull, last_np, o));
         }
         // ---- candidate table: shared memory when it fits, else this warp's global one ----
+        // (sized for the distinct candidates when k_read_cost counted them, else
+        // for every hit)
         uint32_t cap = 64;
-        while (cap < 2u * H) cap <<= 1;
+        const uint32_t hb = (a.read_nd && a.read_nd[r] < H) ? a.read_nd[r] : H;
+        while (cap < 2u * hb) cap <<= 1;
         CandSlot* tab;
         HitRec* hits;
         uint32_t* dense;
@@ -1036,6 +1133,188 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                 return true;
             };
 
+            if constexpr (WAVE) {
+            // Wave mode (see wave_helper): steps of Algorithm 1 taken ahead of their
+            // scores, W picks at a time, then replayed in order.
+            const int W = (int)(blockDim.x >> 5);
+            // the votes of seed record `rec`: added (new candidates listed in
+            // dense), or taken back (undo = true) after a drain started earlier
+            auto seed_votes = [&](const SeedRec& rec, bool undo) {
+                const int o = rec.offset;
+                const int tot = (int)rec.fwd_n + rec.rc_n;
+                for (int j0 = 0; j0 < tot; j0 += 32) {
+                    const int j = j0 + lane;
+                    bool ins = false;
+                    uint32_t slot = 0;
+                    if (j < tot) {
+                        const bool fwd = j < rec.fwd_n;
+                        uint32_t l;
+                        if (fwd) {
+                            l = (rec.flags & kSeedFwdInline)
+                                    ? rec.fwd_ref : __ldg(a.positions + rec.fwd_ref + j);
+                        } else {
+                            const int jj = j - rec.fwd_n;
+                            l = (rec.flags & kSeedRcInline)
+                                    ? rec.rc_ref : __ldg(a.positions + rec.rc_ref + jj);
+                        }
+                        const long long p = fwd ? (long long)l - o : (long long)l - (m - o - s);
+                        if (p >= 0) {
+                            const unsigned long long key =
+                                2ull * (unsigned long long)p + (fwd ? 0 : 1);
+                            if (undo) {
+                                const uint32_t sl = table_find(tab, cap - 1, key);
+                                if (sl != kNoPick)
+                                    atomicSub(&tab[sl].votes, 1u);
+                                else
+                                    atomicOr(a.status, kStInternal);  // cannot happen
+                            } else {
+                                wc.list_entries += (rec.flags & kSeedFwdInline) ? 0u : 1u;
+                                slot = table_add(tab, cap - 1, key, a.status, &ins);
+                            }
+                        }
+                    }
+                    if (!undo) {
+                        const unsigned nb = __ballot_sync(kFull, ins);
+                        if (ins) dense[nd + __popc(nb & ((1u << lane) - 1))] = slot;
+                        nd += __popc(nb);
+                    }
+                }
+                __syncwarp();
+            };
+            bool draining = false;
+            int i = 0;
+            for (;;) {
+                // ---- build: one step per non-popular seed (in the drain, per pick) ----
+                const int Lb = min(d_best, dmax) + c - 1;  // bounds every limit below
+                int w = 0, ns = 0;
+                uint32_t st_slot = kNoPick;  // step `lane`: its pick (or none), t and i after it
+                unsigned long long st_key = 0;
+                int st_t = 0, st_i = 0;
+                bool seeds_over = false;
+                while (w < W && ns < 32) {
+                    if (!draining) {
+                        while (i < n && (wm.seeds[i].flags & kSeedPopular) != 0) ++i;
+                        if (i >= n) {
+                            seeds_over = true;
+                            break;
+                        }
+                        const SeedRec rec = wm.seeds[i++];
+                        any_nonpopular = true;
+                        seed_votes(rec, false);
+                        if (rec.flags & kSeedCountT) ++t;
+                    }
+                    const unsigned long long pk = table_pick(tab, dense, nd, lane);
+                    if (!pk && draining) break;  // the drain has scored everything
+                    uint32_t slot = kNoPick;
+                    unsigned long long key = 0;
+                    if (pk) {
+                        slot = (uint32_t)(pk & 0xfffffu);
+                        key = kKeyMask - ((pk >> 20) & kKeyMask);
+                        if (lane == 0) {
+                            tab[slot].state = kPending;
+                            wm.job[kWaveKeys + 2 * w] = (int)(uint32_t)key;
+                            wm.job[kWaveKeys + 2 * w + 1] = (int)(uint32_t)(key >> 32);
+                        }
+                        ++w;
+                    }
+                    if (lane == ns) {
+                        st_slot = slot;
+                        st_key = key;
+                        st_t = t;
+                        st_i = i;
+                    }
+                    ++ns;
+                    __syncwarp();
+                }
+                if (ns == 0) break;  // seeds used up, or the drain is over
+                // ---- the wave's distances at Lb, one warp each ----
+                if (w > 0 && Lb >= 0) {
+                    // q-gram maps of the strands this wave needs, before any warp counts
+                    if (wm.qbits && use_qfilter(m, Lb)) {
+                        int need = 0;
+                        for (int e = 0; e < w; ++e)
+                            need |= 1 << (wm.job[kWaveKeys + 2 * e] & 1);
+                        for (int sd = 0; sd < 2; ++sd) {
+                            if ((need >> sd) & 1 && !(qbuilt & (1 << sd))) {
+                                build_qbits(sd ? wm.Xr : wm.Xf, m, wm.qbits + sd * kQWords, lane);
+                                qbuilt |= 1 << sd;
+                            }
+                        }
+                    }
+                    if (lane == 0) {
+                        wm.job[0] = kJobDistance;
+                        wm.job[1] = w;
+                        wm.job[2] = Lb;
+                        wm.job[3] = m;
+                    }
+                    __syncthreads();  // wave posted
+                    const unsigned long long key0 =
+                        (unsigned long long)(uint32_t)wm.job[kWaveKeys] |
+                        ((unsigned long long)(uint32_t)wm.job[kWaveKeys + 1] << 32);
+                    const int sd0 = (int)(key0 & 1);
+                    const int d0 = wave_distance(a, sd0 ? wm.Xr : wm.Xf, m, key0, Lb, wm.Tw, wm.lvA,
+                                                 wm.lvB, wm.qbits ? wm.qbits + sd0 * kQWords : nullptr,
+                                                 lane, wc);
+                    if (lane == 0) wm.job[kWaveRes] = d0;
+                    __syncthreads();  // results in
+                }
+                // ---- replay the steps in order ----
+                bool stop = false;
+                int e = 0;  // wave entry of the next pick
+                for (int sx = 0; sx < ns; ++sx) {
+                    const uint32_t slot = __shfl_sync(kFull, st_slot, sx);
+                    const unsigned long long key = __shfl_sync(kFull, st_key, sx);
+                    const int ts = __shfl_sync(kFull, st_t, sx);
+                    const int is = __shfl_sync(kFull, st_i, sx);
+                    if (slot != kNoPick) {
+                        const int L = limit();
+                        int d = kOver;
+                        if (L >= 0) {
+                            if (L > Lb && lane == 0) atomicOr(a.status, kStInternal);  // cannot happen
+                            const int dw = Lb >= 0 ? wm.job[kWaveRes + e] : kOver;
+                            d = (dw >= 0 && dw <= L) ? dw : kOver;
+                            if (lane == 0) {
+                                wc.ed_calls++;
+                                wc.ed_over += (d < 0);
+                            }
+                        }
+                        record(slot, key, d);
+                        ++e;
+                    }
+                    if (draining) continue;
+                    if (d_best < c && d_second < d_best + c) {
+                        returned = true;
+                        stop = true;
+                        break;
+                    }
+                    if (ts >= d_best + c) {
+                        draining = true;
+                        if (sx + 1 < ns) {
+                            // undo the later steps: picks unscored again, votes taken back
+                            for (int sy = sx + 1; sy < ns; ++sy) {
+                                const uint32_t sl = __shfl_sync(kFull, st_slot, sy);
+                                const int iy = __shfl_sync(kFull, st_i, sy);
+                                if (sl != kNoPick && lane == 0) tab[sl].state = kUnscored;
+                                __syncwarp();
+                                seed_votes(wm.seeds[iy - 1], true);
+                            }
+                            // candidates with no votes left do not exist at this step
+                            for (int j = lane; j < nd; j += 32) {
+                                const uint32_t sl = dense[j];
+                                if (tab[sl].votes == 0 && tab[sl].state == kUnscored)
+                                    tab[sl].state = kRetired;
+                            }
+                            __syncwarp();
+                            t = ts;
+                            i = is;
+                        }
+                        break;
+                    }
+                }
+                if (stop) break;
+                if (seeds_over && !draining) break;  // Algorithm 1's seed loop is over
+            }
+            } else {
             // One pass per non-popular seed: add its votes, pick and score one
             // candidate, test the exits.  Once the Baeza-Yates test passes the loop
             // only picks and scores (no early return) until nothing is left.
@@ -1109,6 +1388,7 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                     if (t >= d_best + c) draining = true;
                 }
             }
+            }  // WAVE
             const bool all_popular = !any_nonpopular;  // n >= 1 here
             if (!returned && d_best <= dmax && d_second >= d_best + c) {
                 res_cls = SNAP_SINGLE_HIT;
@@ -1223,6 +1503,217 @@ __global__ void __launch_bounds__(kTeamWarps * 32) k_align_team(FusedArgs a) {
     flush_counters(a.ctr, wc);
 }
 
+// Wave mode (see wave_helper): one read per block at a time, blockDim.x / 32
+// warps (2 to 8), each with its own window and diagonal buffers after the lead's
+// layout, then the job words.  Plain index and first_seeds <= 1 only.
+__global__ void __launch_bounds__(kWaveMaxWarps * 32) k_align_wave(FusedArgs a) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int W = (int)(blockDim.x >> 5);
+    WarpMem wm;
+    wm.Xf = smem;
+    wm.Xr = smem + a.off_xr;
+    wm.Tw = smem + a.off_tw;
+    wm.seeds = a.gseeds ? a.gseeds + (uint64_t)blockIdx.x * a.seed_cap
+                        : reinterpret_cast<SeedRec*>(smem + a.off_seeds);
+    wm.stab = reinterpret_cast<CandSlot*>(smem + a.off_tab);
+    wm.shits = reinterpret_cast<HitRec*>(smem + a.off_hits);
+    wm.sdense = smem + a.off_dense;
+    wm.lvA = reinterpret_cast<int*>(smem + a.off_lv);
+    wm.lvB = wm.lvA + a.lv_ints / 2;
+    const uint64_t gw = blockIdx.x;
+    wm.gtab = a.gtab ? a.gtab + gw * a.gcap : nullptr;
+    wm.ghits = a.ghits ? a.ghits + gw * (a.gcap / 2) : nullptr;
+    wm.gdense = a.gdense ? a.gdense + gw * (a.gcap / 2) : nullptr;
+    wm.qbits = a.gqbits ? a.gqbits + gw * (2 * kQWords) : nullptr;
+    wm.job = reinterpret_cast<int*>(smem + a.warp_words + (size_t)(W - 1) * (a.wt + a.lv_ints));
+    wm.par = nullptr;
+    WarpCounters wc;
+    if (wib != 0) {
+        wave_helper(a, wm, smem, wib, wc);
+        flush_counters(a.ctr, wc);
+        return;
+    }
+    for (int j = lane; j < a.scap; j += 32) wm.stab[j] = empty_slot();
+    __syncwarp();
+    const unsigned long long n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(a.head, 1ull);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= n_items) break;
+        const uint64_t r = a.order ? a.order[it] : it;
+        align_one_read<0, false, false, true>(a, wm, r, lane, wc);
+    }
+    if (lane == 0) wm.job[0] = kJobExit;
+    __syncthreads();  // releases the helpers
+    flush_counters(a.ctr, wc);
+}
+
+// ---------------------------------------------------------------------------
+// Read order of a block-per-read class.  A block aligns one read at a time and
+// a read's cost grows with the candidates Algorithm 1 scores (one pick per
+// non-popular seed while unscored candidates remain), so a few repeat-rich
+// reads can outlast the rest of the launch.  k_read_cost estimates each read's
+// picks as min(non-popular seeds, distinct candidates over all seeds) from its
+// probes alone, and k_order_by_cost lists the class's reads by that estimate,
+// largest first (longest-processing-time order).  The distinct count also
+// bounds the read's candidate table, which then often fits in shared memory
+// where its hit count does not.  Results do not depend on either.
+// ---------------------------------------------------------------------------
+constexpr int kCostWarps = 4;
+constexpr int kCostSlots = 1024;  // per-warp key set; counting stops past half of it
+constexpr uint32_t kNoCount = 0xffffffffu;
+constexpr int kCostBuckets = 1024;
+
+struct CostArgs {
+    const uint64_t* offsets;
+    uint64_t n;
+    const uint32_t* rwords;
+    uint64_t base0;
+    int s, num_seeds, h_max;
+    uint8_t shifts[32];
+    int n_shifts;
+    const IndexSlot* slots;
+    uint64_t T;
+    const uint32_t* positions;
+    int* status;
+    unsigned mask;     // length classes whose reads are counted
+    uint32_t* cost;    // per read: min(non-popular seeds, distinct candidates, buckets - 1)
+    uint32_t* read_nd; // per read: distinct candidates, or kNoCount past kCostSlots / 2
+    unsigned* need;    // per class: the largest table need (distinct count, else hits)
+};
+
+// One warp per read of the batch whose length class is in `mask`.
+__global__ void __launch_bounds__(kCostWarps * 32) k_read_cost(CostArgs a) {
+    __shared__ unsigned long long sets[kCostWarps * kCostSlots];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned long long* hs = sets + wib * kCostSlots;
+    for (int j = lane; j < kCostSlots; j += 32) hs[j] = kEmptyKey;
+    __syncwarp();
+    uint32_t steps = 0;
+    for (uint64_t r = (uint64_t)blockIdx.x * kCostWarps + wib; r < a.n;
+         r += (uint64_t)gridDim.x * kCostWarps) {
+        const uint64_t o0 = a.offsets[r];
+        const int m = (int)(a.offsets[r + 1] - o0);
+        const int q = length_class((uint64_t)m);
+        if (!((a.mask >> q) & 1u)) continue;
+        const uint64_t rb = o0 - a.base0 + kReadPadBases;
+        const int s = a.s;
+        int ng = 0;
+        if (m >= s) {
+            ng = a.num_seeds > 0 ? a.num_seeds : m / s;
+            ng = min(ng, m - s + 1);
+        }
+        int nnp = 0, nd = 0;
+        unsigned H = 0;  // hits of the non-popular seeds, as the align kernels count them
+        bool full = false;
+        for (int i0 = 0; i0 < ng; i0 += 32) {
+            const int i = i0 + lane;
+            SeedRec rec;
+            rec.flags = 0;
+            rec.fwd_n = rec.rc_n = 0;
+            rec.fwd_ref = rec.rc_ref = 0;
+            rec.offset = 0;
+            bool np = false;
+            if (i < ng) {
+                bool p0 = false;
+                const int o = seed_offset(i, m, s, a.shifts, a.n_shifts, &p0);
+                const uint64_t v = get32(a.rwords, rb + (uint64_t)o) & kmer_mask(s);
+                uint32_t cnt = 0;
+                lookup_seed(a.slots, a.T, a.positions, v, s, &rec, &cnt, a.status, &steps);
+                rec.offset = (uint16_t)o;
+                np = cnt <= (uint32_t)a.h_max;
+            }
+            unsigned hsum = np ? (unsigned)rec.fwd_n + rec.rc_n : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) hsum += __shfl_xor_sync(kFull, hsum, o);
+            H += hsum;
+            const unsigned npm = __ballot_sync(kFull, np);
+            nnp += __popc(npm);
+            for (unsigned mm = npm; mm && !full; mm &= mm - 1) {
+                const int src = __ffs(mm) - 1;
+                const uint32_t fref = __shfl_sync(kFull, rec.fwd_ref, src);
+                const uint32_t rref = __shfl_sync(kFull, rec.rc_ref, src);
+                const int fn = __shfl_sync(kFull, (int)rec.fwd_n, src);
+                const int tot = fn + __shfl_sync(kFull, (int)rec.rc_n, src);
+                const int o = __shfl_sync(kFull, (int)rec.offset, src);
+                const int fl = __shfl_sync(kFull, (int)rec.flags, src);
+                for (int j0 = 0; j0 < tot && !full; j0 += 32) {
+                    const int j = j0 + lane;
+                    bool ins = false;
+                    if (j < tot) {
+                        const bool fwd = j < fn;
+                        const uint32_t l = fwd ? ((fl & kSeedFwdInline) ? fref
+                                                                        : __ldg(a.positions + fref + j))
+                                               : ((fl & kSeedRcInline) ? rref
+                                                                       : __ldg(a.positions + rref + j - fn));
+                        const long long p = fwd ? (long long)l - o : (long long)l - (m - o - s);
+                        if (p >= 0) {
+                            const unsigned long long key = 2ull * (unsigned long long)p + (fwd ? 0 : 1);
+                            uint32_t h = (uint32_t)mix64(key) & (kCostSlots - 1);
+                            for (int step = 0; step < kCostSlots; ++step) {
+                                const unsigned long long prev = atomicCAS(&hs[h], kEmptyKey, key);
+                                if (prev == kEmptyKey) ins = true;
+                                if (prev == kEmptyKey || prev == key) break;
+                                h = (h + 1) & (kCostSlots - 1);
+                            }
+                        }
+                    }
+                    nd += __popc(__ballot_sync(kFull, ins));
+                    full = nd > kCostSlots / 2;  // so the set never holds more than 544 keys
+                }
+            }
+        }
+        if (lane == 0) {
+            const int est = full ? nnp : min(nnp, nd);
+            a.cost[r] = (uint32_t)min(est, kCostBuckets - 1);
+            a.read_nd[r] = full ? kNoCount : (uint32_t)nd;
+            atomicMax(a.need + q, full ? H : (unsigned)nd);
+        }
+        __syncwarp();
+        for (int j = lane; j < kCostSlots; j += 32) hs[j] = kEmptyKey;
+        __syncwarp();
+    }
+}
+
+// One block of kScanThreads: out = the *count ids of `in` ordered by cost,
+// largest first (ties in any order).
+__global__ void __launch_bounds__(kScanThreads) k_order_by_cost(const uint32_t* in, uint32_t* out,
+                                                                 const unsigned long long* count,
+                                                                 const uint32_t* cost) {
+    constexpr int kPer = kCostBuckets / kScanThreads;
+    __shared__ uint32_t cur[kCostBuckets];
+    __shared__ uint32_t wsum[kScanThreads / 32];
+    const int tid = threadIdx.x;
+    const unsigned long long n = *count;
+    for (int b = tid; b < kCostBuckets; b += kScanThreads) cur[b] = 0;
+    __syncthreads();
+    // bucket kCostBuckets - 1 - cost: the scan then lays the largest costs out first
+    for (unsigned long long it = tid; it < n; it += kScanThreads)
+        atomicAdd(&cur[kCostBuckets - 1 - min(cost[in[it]], (uint32_t)(kCostBuckets - 1))], 1u);
+    __syncthreads();
+    uint32_t mine[kPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        mine[k] = cur[tid * kPer + k];
+        sum += mine[k];
+    }
+    uint32_t total;
+    uint32_t start = block_exclusive_scan(sum, wsum, &total);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        cur[tid * kPer + k] = start;
+        start += mine[k];
+    }
+    __syncthreads();
+    for (unsigned long long it = tid; it < n; it += kScanThreads) {
+        const uint32_t id = in[it];
+        const uint32_t b = kCostBuckets - 1 - min(cost[id], (uint32_t)(kCostBuckets - 1));
+        out[atomicAdd(&cur[b], 1u)] = id;
+    }
+}
+
 using FusedKernel = void (*)(FusedArgs);
 
 // The kernel variant for a batch whose largest limit is Lmax: one or two
@@ -1245,7 +1736,7 @@ static bool param_variant(const snap_index* idx, const snap_params* p) {
 }
 
 static bool is_team_kernel(FusedKernel k) {
-    return k == k_align_team<false> || k == k_align_team<true>;
+    return k == k_align_team<false> || k == k_align_team<true> || k == k_align_wave;
 }
 
 // ---------------------------------------------------------------------------
@@ -1314,7 +1805,8 @@ void engine_destroy(Engine* e) {
     for (DevBuf& b : e->gseeds) b.release();
     for (DevBuf& b : e->gqbits) b.release();
     for (DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->gdense,
-                      &e->heavy, &e->hseeds, &e->hprobed, &e->h_reads, &e->h_offsets, &e->h_out,
+                      &e->heavy, &e->hseeds, &e->hprobed, &e->rcost, &e->rnd, &e->order2,
+                      &e->cneed, &e->h_reads, &e->h_offsets, &e->h_out,
                       &e->h_dmax, &e->p_seeds,
                       &e->p_hits,
                       &e->p_hitoff, &e->p_partial, &e->p_table, &e->p_events, &e->p_hitlist,
@@ -1327,6 +1819,11 @@ void engine_destroy(Engine* e) {
         if (ev) cudaEventDestroy(ev);
     for (auto& ev : e->tev)
         if (ev) cudaEventDestroy(ev);
+    for (auto& ev : e->ev_join)
+        if (ev) cudaEventDestroy(ev);
+    if (e->ev_fork) cudaEventDestroy(e->ev_fork);
+    for (auto& st : e->aux)
+        if (st) cudaStreamDestroy(st);
     if (e->gexec) cudaGraphExecDestroy(e->gexec);
     if (e->own_stream) cudaStreamDestroy(e->own_stream);
     delete e;
@@ -1337,8 +1834,9 @@ size_t engine_bytes(const Engine* e) {
     for (const DevBuf& b : e->gseeds) s += b.bytes;
     for (const DevBuf& b : e->gqbits) s += b.bytes;
     for (const DevBuf* b : {&e->stats, &e->head, &e->packed, &e->gtab, &e->ghits, &e->gdense,
-                            &e->heavy, &e->hseeds, &e->hprobed,
-                            &e->h_reads, &e->h_offsets, &e->h_out, &e->h_dmax, &e->p_seeds,
+                            &e->heavy, &e->hseeds, &e->hprobed, &e->rcost, &e->rnd, &e->order2,
+                            &e->cneed, &e->h_reads, &e->h_offsets, &e->h_out, &e->h_dmax,
+                            &e->p_seeds,
                             &e->p_hits, &e->p_hitoff, &e->p_partial, &e->p_table, &e->p_events,
                             &e->p_hitlist, &e->p_items, &e->p_misc, &e->p_dense})
         s += b->bytes;
@@ -1354,7 +1852,7 @@ void engine_release(Engine* e) {
     }
     e->gtab_ready = false;
     for (DevBuf* b : {&e->packed, &e->gtab, &e->ghits, &e->gdense, &e->heavy, &e->hseeds,
-                      &e->hprobed, &e->h_reads,
+                      &e->hprobed, &e->rcost, &e->rnd, &e->order2, &e->cneed, &e->h_reads,
                       &e->h_offsets,
                       &e->h_out, &e->h_dmax, &e->p_seeds, &e->p_hits, &e->p_hitoff, &e->p_partial,
                       &e->p_table, &e->p_events, &e->p_hitlist, &e->p_items, &e->p_misc, &e->p_dense})
@@ -1531,6 +2029,8 @@ static int finish_status(Engine* e, cudaStream_t stream, const char* where, uint
     L.table_slots = e->last_shape.scap;
     L.graph_replay = e->last_graph;
     L.team_classes = e->last_team;
+    L.wave_classes = e->last_wave;
+    L.wave_warps = e->last_wave_warps;
     L.probe_ms = L.distance_ms = 0;
     L.host_plan_ms = e->host_plan_ms;
     L.reads_light = h->ctr_light.reads_done;
@@ -1566,7 +2066,70 @@ struct BatchPlan {
     uint32_t* heavy_ids = nullptr;
     unsigned long long* head = nullptr;  // [0..3] class queue heads, [4] leftovers, [5..8] class counts
     uint64_t table_slots[kClasses] = {0, 0, 0, 0};  // global candidate slots each class needs
+    bool ordered[kClasses] = {false, false, false, false};  // k_read_cost + k_order_by_cost first
+    const uint32_t* unsorted[kClasses] = {nullptr, nullptr, nullptr, nullptr};
+    uint32_t* rcost = nullptr;
+    uint32_t* rnd = nullptr;
+    bool concurrent = false;  // class launches side by side (disjoint global tables)
 };
+
+// Whether class q aligns one read per block (team or wave mode): its limits
+// exceed 31 and (chosen per batch) it has fewer than max(8, longest read / 12)
+// reads per SM, where per-read work, growing with the square of the limit, would
+// leave one warp per read latency-bound; e->team: -1 per batch, 0 never, >= 1 always.
+static bool block_per_read(const Engine* e, const BatchPrep& bp, int q) {
+    const int mmax = std::max(1u, bp.st.cls_max_len[q]);
+    const int Lmax = std::max(0, bp.st.cls_max_L0[q]);
+    const uint64_t team_below = (uint64_t)e->sms * std::max(kTeamReadsPerSm, mmax / 12);
+    return Lmax > 31 && (e->team < 0 ? bp.st.cls_n[q] < team_below : e->team >= 1);
+}
+
+// k_read_cost over the reads of the block-per-read classes (plain index,
+// first_seeds <= 1): per-read cost keys and distinct-candidate counts on the
+// device, each class's largest table need on the host (e->cost_need).
+static int count_candidates(const snap_index* idx, Engine* e, const uint64_t* d_offsets,
+                            uint64_t n, const snap_params* p, cudaStream_t stream,
+                            const BatchPrep& bp) {
+    int rc;
+    e->cost_mask = 0;
+    if (param_variant(idx, p)) return SNAP_OK;
+    for (int q = 0; q < kClasses; ++q)
+        if (bp.st.cls_n[q] && block_per_read(e, bp, q)) e->cost_mask |= 1u << q;
+    if (!e->cost_mask) return SNAP_OK;
+    if ((rc = e->rcost.ensure(n * sizeof(uint32_t), "read costs"))) return rc;
+    if ((rc = e->rnd.ensure(n * sizeof(uint32_t), "candidate counts"))) return rc;
+    if ((rc = e->cneed.ensure(kClasses * sizeof(unsigned), "table needs"))) return rc;
+    SNAP_CUDA(cudaMemsetAsync(e->cneed.p, 0, kClasses * sizeof(unsigned), stream), "need clear");
+    CostArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    ca.offsets = d_offsets;
+    ca.n = n;
+    ca.rwords = bp.rwords;
+    ca.base0 = bp.base0;
+    ca.s = idx->s;
+    ca.num_seeds = p->num_seeds;
+    ca.h_max = p->max_hits;
+    shift_list(idx->s, ca.shifts, &ca.n_shifts);
+    ca.slots = idx->slots;
+    ca.T = idx->T;
+    ca.positions = idx->positions;
+    ca.status = &static_cast<BatchStats*>(e->stats.p)->status;
+    ca.mask = e->cost_mask;
+    ca.cost = static_cast<uint32_t*>(e->rcost.p);
+    ca.read_nd = static_cast<uint32_t*>(e->rnd.p);
+    ca.need = static_cast<unsigned*>(e->cneed.p);
+    const unsigned blocks = (unsigned)std::max<uint64_t>(
+        1, std::min<uint64_t>((uint64_t)e->sms * 16, (n + kCostWarps - 1) / kCostWarps));
+    e->launches++;
+    k_read_cost<<<blocks, kCostWarps * 32, 0, stream>>>(ca);
+    SNAP_CUDA(cudaGetLastError(), "cost launch");
+    unsigned* h_need = reinterpret_cast<unsigned*>(static_cast<char*>(e->pin.p) + 3200);
+    SNAP_CUDA(cudaMemcpyAsync(h_need, e->cneed.p, kClasses * sizeof(unsigned),
+                              cudaMemcpyDeviceToHost, stream), "need copy");
+    SNAP_CUDA(cudaStreamSynchronize(stream), "snap_align");
+    for (int q = 0; q < kClasses; ++q) e->cost_need[q] = h_need[q];
+    return SNAP_OK;
+}
 
 // Lay out the warp kernel of class q; allocate what it needs (no allocation
 // happens after planning, so the enqueue can be captured).
@@ -1612,8 +2175,8 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     // many seeds (long reads): seed records in global memory, more warps per SM
     const bool seeds_global = nmax > 64;
     const int seed_words = seeds_global ? 0 : 4 * a.seed_cap;
-    const uint64_t team_below = (uint64_t)e->sms * std::max(kTeamReadsPerSm, mmax / 12);
-    const bool team = Lmax > 31 && (e->team < 0 ? bp.st.cls_n[q] < team_below : e->team == 1);
+    const bool team = block_per_read(e, bp, q);
+    const bool ordered = (e->cost_mask >> q) & 1u;  // counted by k_read_cost
     const int pwords = (Lmax <= 31 && !team) ? par_words(mmax) : 0;  // register-diagonal kernels
     const int fixed_words = 2 * a.wx + a.wt + seed_words + a.lv_ints + pwords;
     const int budget_words = 200 * 1024 / 4;  // per block; 7 words per table slot
@@ -1625,6 +2188,13 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     while (warps > 1 && bp.st.cls_n[q] < (uint64_t)e->sms * warps) warps >>= 1;
     while (warps > 1 && warps * (fixed_words + 7 * 64) > budget_words) warps >>= 1;
     int scap = std::max(64, shape.scap);
+    if (ordered) {
+        // room in shared memory for the largest distinct-candidate count of the
+        // class, up to 1024 slots (one table per block in this mode)
+        uint32_t want = 64;
+        while (want < 2u * std::min(e->cost_need[q], 512u)) want <<= 1;
+        scap = std::max(scap, (int)want);
+    }
     while (scap > 64 && warps * (fixed_words + 7 * scap) > budget_words) scap >>= 1;
     a.scap = scap;
     a.off_xr = a.wx;
@@ -1642,7 +2212,31 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
         set_error("snap_align: internal shared-memory layout is not 16-byte aligned");
         return SNAP_E_INTERNAL;
     }
-    const size_t smem = (size_t)warps * a.warp_words * 4 + (team ? kJobWords * 4 : 0);
+    size_t smem = (size_t)warps * a.warp_words * 4 + (team ? kJobWords * 4 : 0);
+    const bool variant = param_variant(idx, p);
+    // wave mode (asked for with team = 2): the number of warps (candidates per
+    // wave) that puts the most warps on an SM, at most kWaveMaxWarps, ties to
+    // more per block
+    int wave_warps = 0;
+    if (team && !variant && e->team == 2) {
+        int best = 0;
+        for (int W = kWaveMaxWarps; W >= 2; W >>= 1) {
+            const size_t b = ((size_t)a.warp_words + (size_t)(W - 1) * (a.wt + a.lv_ints) +
+                              kWaveJobWords) * 4;
+            if (b > 227 * 1024) continue;
+            if ((rc = raise_smem_limit((const void*)k_align_wave, b))) return rc;
+            int per_sm = 0;
+            SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_align_wave, W * 32, b),
+                      "occupancy");
+            if (per_sm * W > best) {
+                best = per_sm * W;
+                wave_warps = W;
+            }
+        }
+        if (wave_warps)
+            smem = ((size_t)a.warp_words + (size_t)(wave_warps - 1) * (a.wt + a.lv_ints) +
+                    kWaveJobWords) * 4;
+    }
     if (smem > 227 * 1024) {
         set_error("snap_align: read length %d needs %zu bytes of shared memory per warp", mmax,
                   (size_t)a.warp_words * 4);
@@ -1653,10 +2247,10 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     bool qmaps = false;
     for (int L = kQMinL; L <= Lmax && !qmaps; ++L)
         qmaps = use_qfilter(std::min(mmax, L * L / 8 - L), L);
-    const bool variant = param_variant(idx, p);
-    const FusedKernel kfn = team ? (variant ? k_align_team<true> : k_align_team<false>)
-                                 : fused_kernel_for(Lmax, qmaps, variant);
-    const int threads = team ? kTeamWarps * 32 : warps * 32;
+    const FusedKernel kfn = wave_warps ? k_align_wave
+                            : team     ? (variant ? k_align_team<true> : k_align_team<false>)
+                                       : fused_kernel_for(Lmax, qmaps, variant);
+    const int threads = wave_warps ? wave_warps * 32 : team ? kTeamWarps * 32 : warps * 32;
     if ((rc = raise_smem_limit((const void*)kfn, smem))) return rc;
     int per_sm = 0;
     SNAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem),
@@ -1666,7 +2260,9 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     const uint64_t need_blocks = (bp.st.cls_n[q] + warps - 1) / warps;
     if (blocks > need_blocks) blocks = std::max<uint64_t>(1, need_blocks);
     // global overflow tables for reads whose candidate table outgrows shared memory
-    const uint64_t hb = bp.st.cls_max_hits[q];
+    // (sized for the class's largest hit count, or its largest distinct count when
+    // k_read_cost counted it)
+    const uint64_t hb = ordered ? (uint64_t)e->cost_need[q] : bp.st.cls_max_hits[q];
     uint64_t gcap = 64;
     while (gcap < 2 * hb) gcap <<= 1;
     if (gcap > kMaxTableSlots) {
@@ -1700,6 +2296,8 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
             return rc;
         a.gseeds = static_cast<SeedRec*>(gs.p);
     }
+    // a block-per-read class runs its reads largest estimate first (k_read_cost)
+    plan->ordered[q] = ordered;
     plan->kfn[q] = kfn;
     plan->smem[q] = smem;
     plan->blocks[q] = blocks;
@@ -1740,10 +2338,36 @@ static int plan_batch(const snap_index* idx, Engine* e, const uint64_t* d_offset
         plan->a[q].hseeds = plan->light ? static_cast<const SeedRec*>(e->hseeds.p) : nullptr;
         plan->a[q].hprobed = plan->light ? static_cast<const uint8_t*>(e->hprobed.p) : nullptr;
     }
-    // global candidate tables: one buffer for the largest class need (the class
-    // launches run one after another and leave the tables empty)
-    uint64_t slots = 0;
-    for (int q = 0; q < kClasses; ++q) slots = std::max(slots, plan->table_slots[q]);
+    bool any_ordered = false;
+    for (int q = 0; q < kClasses; ++q) any_ordered |= plan->use[q] && plan->ordered[q];
+    if (any_ordered) {
+        if ((rc = e->rcost.ensure(n * sizeof(uint32_t), "read costs"))) return rc;
+        if ((rc = e->rnd.ensure(n * sizeof(uint32_t), "candidate counts"))) return rc;
+        if ((rc = e->order2.ensure(n * sizeof(uint32_t), "ordered read lists"))) return rc;
+        plan->rcost = static_cast<uint32_t*>(e->rcost.p);
+        plan->rnd = static_cast<uint32_t*>(e->rnd.p);
+        for (int q = 0; q < kClasses; ++q) {
+            if (!plan->use[q] || !plan->ordered[q]) continue;
+            plan->unsorted[q] = plan->cl.list + plan->cl.off[q];
+            plan->a[q].order = static_cast<uint32_t*>(e->order2.p) + plan->cl.off[q];
+            plan->a[q].read_nd = plan->rnd;
+        }
+    }
+    // global candidate tables: the class launches run side by side when two or
+    // more classes are present and their tables fit the budget together (each
+    // class its own slice), else one after another sharing one buffer for the
+    // largest need; kernels leave their tables empty
+    const uint64_t slot_bytes = sizeof(CandSlot) + sizeof(HitRec) / 2 + sizeof(uint32_t) / 2;
+    int nuse = 0, ntab = 0;
+    uint64_t slots_sum = 0, slots_max = 0;
+    for (int q = 0; q < kClasses; ++q) {
+        nuse += plan->use[q];
+        ntab += plan->table_slots[q] > 0;
+        slots_sum += plan->table_slots[q];
+        slots_max = std::max(slots_max, plan->table_slots[q]);
+    }
+    plan->concurrent = nuse >= 2 && (ntab <= 1 || slots_sum * slot_bytes <= e->overflow_budget);
+    const uint64_t slots = plan->concurrent ? slots_sum : slots_max;
     if (slots) {
         void* before = e->gtab.p;
         const size_t before_bytes = e->gtab.bytes;
@@ -1758,11 +2382,13 @@ static int plan_batch(const snap_index* idx, Engine* e, const uint64_t* d_offset
             SNAP_CUDA(cudaGetLastError(), "table init");
             e->gtab_ready = true;
         }
+        uint64_t at = 0;  // this class's first slot
         for (int q = 0; q < kClasses; ++q) {
             if (!plan->table_slots[q]) continue;
-            plan->a[q].gtab = static_cast<CandSlot*>(e->gtab.p);
-            plan->a[q].ghits = static_cast<HitRec*>(e->ghits.p);
-            plan->a[q].gdense = static_cast<uint32_t*>(e->gdense.p);
+            plan->a[q].gtab = static_cast<CandSlot*>(e->gtab.p) + at;
+            plan->a[q].ghits = static_cast<HitRec*>(e->ghits.p) + at / 2;
+            plan->a[q].gdense = static_cast<uint32_t*>(e->gdense.p) + at / 2;
+            if (plan->concurrent) at += plan->table_slots[q];
         }
     }
     return SNAP_OK;
@@ -1788,13 +2414,45 @@ static int enqueue_batch(const snap_index* idx, Engine* e, const uint64_t* d_off
     k_split_classes<<<grid_cap(e->sms, n, 256), 256, 0, stream>>>(
         plan.light ? plan.heavy_ids : nullptr, plan.head + 4, n, d_offsets, plan.cl);
     SNAP_CUDA(cudaGetLastError(), "split launch");
-    for (int q = 0; q < kClasses; ++q) {
-        if (!plan.use[q]) continue;
-        e->launches++;
-        plan.kfn[q]<<<(unsigned)plan.blocks[q], plan.threads[q], plan.smem[q], stream>>>(
-            plan.a[q]);
-        SNAP_CUDA(cudaGetLastError(), "align launch");
+    // the class launches, longest reads first; side by side, the first on the
+    // caller's stream and each other one on its own stream forked from it
+    if (plan.concurrent) {
+        if (!e->ev_fork) {
+            SNAP_CUDA(cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming), "event create");
+            for (int q = 0; q < kClasses; ++q) {
+                SNAP_CUDA(cudaEventCreateWithFlags(&e->ev_join[q], cudaEventDisableTiming),
+                          "event create");
+                SNAP_CUDA(cudaStreamCreateWithFlags(&e->aux[q], cudaStreamNonBlocking),
+                          "stream create");
+            }
+        }
+        SNAP_CUDA(cudaEventRecord(e->ev_fork, stream), "fork");
     }
+    bool forked[kClasses] = {false, false, false, false};
+    bool first = true;
+    for (int q = kClasses - 1; q >= 0; --q) {
+        if (!plan.use[q]) continue;
+        cudaStream_t sq = stream;
+        if (plan.concurrent && !first) {
+            sq = e->aux[q];
+            SNAP_CUDA(cudaStreamWaitEvent(sq, e->ev_fork, 0), "fork");
+            forked[q] = true;
+        }
+        first = false;
+        if (plan.ordered[q]) {
+            e->launches++;
+            k_order_by_cost<<<1, kScanThreads, 0, sq>>>(plan.unsorted[q],
+                                                        const_cast<uint32_t*>(plan.a[q].order),
+                                                        plan.cl.count + q, plan.rcost);
+            SNAP_CUDA(cudaGetLastError(), "order launch");
+        }
+        e->launches++;
+        plan.kfn[q]<<<(unsigned)plan.blocks[q], plan.threads[q], plan.smem[q], sq>>>(plan.a[q]);
+        SNAP_CUDA(cudaGetLastError(), "align launch");
+        if (forked[q]) SNAP_CUDA(cudaEventRecord(e->ev_join[q], sq), "join");
+    }
+    for (int q = 0; q < kClasses; ++q)
+        if (forked[q]) SNAP_CUDA(cudaStreamWaitEvent(stream, e->ev_join[q], 0), "join");
     return SNAP_OK;
 }
 
@@ -1813,6 +2471,7 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
                        const snap_params* p, snap_result* d_out, cudaStream_t stream,
                        const BatchPrep& bp) {
     int rc;
+    if ((rc = count_candidates(idx, e, d_offsets, n, p, stream, bp))) return rc;
     // batches that share the classes present, the limits' register layout, the
     // thread-per-read kernel and the size within a factor of two share a tuned shape
     TuneKey key;
@@ -1868,8 +2527,14 @@ static int align_fused(const snap_index* idx, Engine* e, const uint64_t* d_offse
             e->last_shape.scap = plan.a[q].scap;
             break;
         }
-    e->last_team = 0;
-    for (int q = 0; q < kClasses; ++q) e->last_team += plan.use[q] && is_team_kernel(plan.kfn[q]);
+    e->last_team = e->last_wave = e->last_wave_warps = 0;
+    for (int q = 0; q < kClasses; ++q) {
+        e->last_team += plan.use[q] && is_team_kernel(plan.kfn[q]);
+        if (plan.use[q] && plan.kfn[q] == k_align_wave) {
+            e->last_wave++;
+            e->last_wave_warps = plan.threads[q] / 32;
+        }
+    }
     e->last_light = plan.light;
     e->last_graph = 0;
     if (e->use_graphs && stream != nullptr && stream != cudaStreamLegacy &&
@@ -1939,7 +2604,8 @@ int align_batch_device(const snap_index* idx, Engine* e, const uint8_t* d_reads,
     const char* where = plain ? "snap_align_plain" : "snap_align";
     e->last_shape = LaunchShape{0, 0, 0};  // set again by the batched form
     e->last_graph = 0;
-    e->last_team = 0;
+    e->last_team = e->last_wave = e->last_wave_warps = 0;
+    e->cost_mask = 0;  // set by count_candidates for this call's batched form
     e->last_light = false;
     e->last_plain = plain;
     BatchPrep bp;
@@ -2022,8 +2688,8 @@ extern "C" int snap_index_configure(snap_index* idx, int autotune, int cuda_grap
         set_error("snap_index_configure: index is NULL");
         return SNAP_E_INVAL;
     }
-    if (team < -1 || team > 1) {
-        set_error("snap_index_configure: team must be -1, 0 or 1 (got %d)", team);
+    if (team < -1 || team > 2) {
+        set_error("snap_index_configure: team must be -1, 0, 1 or 2 (got %d)", team);
         return SNAP_E_INVAL;
     }
     std::lock_guard<std::mutex> lock(idx->engine->mu);

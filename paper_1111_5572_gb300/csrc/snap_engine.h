@@ -37,6 +37,17 @@ struct Engine {
     DevBuf gqbits[4];  // per-class per-warp q-gram bitmaps (large limits)
     DevBuf hseeds;     // probe records of the reads the thread-per-read kernel hands over
     DevBuf hprobed;    // per read: 1 when hseeds holds its records
+    DevBuf rcost;      // per read of a block-per-read class: estimated picks (k_read_cost)
+    DevBuf rnd;        // per read of such a class: distinct candidates (or kNoCount)
+    DevBuf order2;     // such classes' read lists, largest estimate first
+    DevBuf cneed;      // per class: the largest candidate-table need k_read_cost found
+    unsigned cost_mask = 0;             // classes of this call counted by k_read_cost
+    unsigned cost_need[4] = {0, 0, 0, 0};  // their table needs, on the host
+    // class launches that run side by side: one stream per class besides the
+    // caller's, forked from and joined into the caller's stream by events
+    cudaStream_t aux[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
     bool gtab_ready = false;  // gtab holds only empty slots
     DevBuf h_reads, h_offsets, h_out, h_dmax;  // device copies for the host-buffer entry points
     PinnedBuf pin;
@@ -53,8 +64,10 @@ struct Engine {
     cudaGraphExec_t gexec = nullptr;
     LaunchShape last_shape{0, 0, 0};
     int last_graph = 0;
-    int last_team = 0;  // classes of the last batch that ran in team mode
-    int team = -1;      // team mode: -1 chosen per batch, 0 never, 1 always
+    int last_team = 0;  // classes of the last batch that ran one read per block
+    int last_wave = 0;  // of those, classes in wave mode
+    int last_wave_warps = 0;
+    int team = -1;      // -1 chosen per batch, 0 warp per read, 1 team mode, 2 wave mode
     bool last_plain = false;  // the last call ran the plain form (pev marks are valid)
     // host clock when the batch statistics arrived, and the planning time after it
     std::chrono::steady_clock::time_point t_stats;

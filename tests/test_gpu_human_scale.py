@@ -132,12 +132,13 @@ def test_c4_mixed_requests_full_genome(human):
     _assert_same(np.array(got, dtype=snap.RESULT_DTYPE), ref, "C4 long reads")
 
 
-@pytest.mark.parametrize("team", [0, 1])
+@pytest.mark.parametrize("team", [0, 1, 2])
 def test_long_reads_full_genome_warp_and_team(human, team):
     """320 reads of 1-10 kb (log-uniform) with the serving recipe's error model and
     limits (d_max = max(8, ceil(0.08 m)), up to 800) on the 3.1 Gbp genome, aligned
-    with one warp per read (team=0) and with a block per read (team=1, every long
-    class), each checked field by field against the oracle."""
+    with one warp per read (team=0), in team mode (team=1) and in wave mode (team=2),
+    the last two for every long class, each checked field by field against the
+    oracle."""
     snap, g, gi = human
     w = synth.CONFIGS["C4"]
     lens = synth.read_lengths(320, 1, 100, 1000, 10000, 0.0, seed=900)
@@ -153,6 +154,7 @@ def test_long_reads_full_genome_warp_and_team(human, team):
     # every length class present has limits above 31, so team=1 puts each in team mode
     classes = {int(m > 256) + int(m > 1024) + int(m > 4096) for m in rd.lengths().tolist()}
     assert st["team_classes"] == (0 if team == 0 else len(classes)), st["team_classes"]
+    assert st["wave_classes"] == (len(classes) if team == 2 else 0), st["wave_classes"]
     keys = oracle.read_seed_kmers(rd.bases, rd.offsets, w.seed_len, w.num_seeds)
     ref, ost = oracle.Index(g, w.seed_len, kmer_filter=keys).align(
         rd.bases, rd.offsets, max_dist_per_read=dpr, threads=16, **w.params())

@@ -416,8 +416,10 @@ def test_c2_full_size_sampled(snap):
 def test_team_mode_equals_warp_mode(snap):
     # Reads of 2.5-4 kb fall in one length class with limits up to 320.  The same
     # batch aligned with one warp per read (team=0), in team mode (team=1: a block
-    # per read, all its warps on each edit distance) and with the per-batch choice
-    # (team=-1) gives identical results, and the oracle agrees on a sample.
+    # per read, all its warps on each edit distance), in wave mode (team=2: a block
+    # per read, each warp on its own candidate of the next picks) and with the
+    # per-batch choice (team=-1, team mode here) gives identical results, and the
+    # oracle agrees on a sample.
     w = synth.CONFIGS["C4"].scaled(G=3_000_000, n_reads=0)
     g, _ = w.make_genome()
     gi = snap.Index(g, w.seed_len)
@@ -426,17 +428,64 @@ def test_team_mode_equals_warp_mode(snap):
     rd = synth.reads(g, lens, w.sub_rate, w.indel_rate, w.indel_len, seed=17)
     dpr = w.max_dist_per_read(rd.lengths())
     runs = {}
-    for team in (0, 1, -1):
+    for team in (0, 1, 2, -1):
         gi.configure(team=team)
         runs[team] = gi.align(rd.bases, rd.offsets, max_dist_per_read=dpr, **w.params())
         st = gi.last_call_stats()
         assert st["team_classes"] == (0 if team == 0 else 1), team
+        assert st["wave_classes"] == (1 if team == 2 else 0), team
         assert st["ed_filtered"] > 0
+        if team == 2:
+            assert st["wave_warps"] in (2, 4, 8), st["wave_warps"]
+    gi.configure(team=-1)
     assert_same(runs[1], runs[0], "team vs warp mode")
+    assert_same(runs[2], runs[0], "wave vs warp mode")
     assert_same(runs[-1], runs[0], "chosen vs warp mode")
     with pytest.raises(snap.SnapError):
-        gi.configure(team=2)
+        gi.configure(team=3)
     j = 40
     ref, _ = oracle.Index(g, w.seed_len).align(rd.bases[:int(rd.offsets[j])], rd.offsets[:j + 1],
                                                max_dist_per_read=dpr[:j], threads=4, **w.params())
     assert_same(runs[1][:j], ref, "team mode vs oracle")
+    assert_same(runs[2][:j], ref, "wave mode vs oracle")
+
+
+@pytest.mark.parametrize("case", ["low_error", "exact_copies"])
+def test_wave_mode_exits(snap, case):
+    # Wave mode takes Algorithm 1's steps ahead of their scores, so its exits are
+    # the cases to check: reads of 1-2 kb with 0.3% errors meet the Baeza-Yates test
+    # (t >= d_best + c) a few seeds in, usually inside a wave, whose later steps are
+    # then undone before the drain; on a genome of exact repeat copies, error-free
+    # reads in copies end early (d_best < c and a second hit within c).  Wave mode
+    # = warp mode = team mode = oracle, read for read.
+    w = synth.CONFIGS["C4"].scaled(G=3_000_000, n_reads=0)
+    if case == "low_error":
+        g, _ = w.make_genome()
+        sub, indel = 0.003, 0.0005
+    else:
+        g, _ = synth.genome(3_000_000, 0.5, divergence=0.0)
+        sub, indel = 0.0, 0.0
+    gi = snap.Index(g, w.seed_len)
+    n = 400
+    lens = np.random.default_rng(11).integers(1000, 2001, n).astype(np.uint32)
+    rd = synth.reads(g, lens, sub, indel, w.indel_len, seed=23)
+    dpr = w.max_dist_per_read(rd.lengths())
+    assert dpr.min() > 31  # every read in a block-per-read class
+    runs = {}
+    try:
+        for team in (0, 1, 2):
+            gi.configure(team=team)
+            runs[team] = gi.align(rd.bases, rd.offsets, max_dist_per_read=dpr, **w.params())
+            if team == 2:
+                assert gi.last_call_stats()["wave_classes"] >= 1
+    finally:
+        gi.configure(team=-1)
+    ref, ost = oracle.Index(g, w.seed_len).align(rd.bases, rd.offsets, max_dist_per_read=dpr,
+                                                 threads=16, **w.params())
+    assert_same(runs[2], ref, f"wave mode vs oracle ({case})")
+    assert_same(runs[0], ref, f"warp mode vs oracle ({case})")
+    assert_same(runs[1], ref, f"team mode vs oracle ({case})")
+    if case == "exact_copies":
+        assert ost.n_multiple > 20, ost.n_multiple
+    else:
+        assert ost.n_single > 200, ost.n_single
