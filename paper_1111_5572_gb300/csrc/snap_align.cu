@@ -1117,17 +1117,30 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) words += __shfl_xor_sync(kFull, words, o);
                     if (lane == 0) wc.window_words += words;
-                    for (int j = 0; j < k; ++j) {
-                        const uint32_t slot = chunk[j];
+                    // a candidate over Lc is over at its own limit and changes nothing
+                    // but its state (written by its lane); only those within Lc are
+                    // replayed in order, each at the limit of its turn, and the ones
+                    // between them are counted at the limit they share
+                    const unsigned within = __ballot_sync(kFull, lane < k && d0 >= 0);
+                    if (lane < k && d0 < 0) tab[chunk[lane]].state = kOver;
+                    int next = 0;  // first position of the chunk not counted yet
+                    for (unsigned mm = within;; mm &= mm - 1) {
+                        const int j = mm ? __ffs(mm) - 1 : k;
+                        const int L = limit();
+                        if (L >= 0 && lane == 0) {
+                            wc.ed_calls += (uint32_t)(j - next);
+                            wc.ed_over += (uint32_t)(j - next);
+                        }
+                        if (!mm) break;
                         const unsigned long long key = __shfl_sync(kFull, my_key, j);
                         const int dj = __shfl_sync(kFull, d0, j);
-                        const int L = limit();
-                        const int d = (L >= 0 && dj >= 0 && dj <= L) ? dj : kOver;
+                        const int d = (L >= 0 && dj <= L) ? dj : kOver;
                         if (L >= 0 && lane == 0) {
                             wc.ed_calls++;
                             wc.ed_over += (d < 0);
                         }
-                        record(slot, key, d);
+                        record(chunk[j], key, d);
+                        next = j + 1;
                     }
                 }
                 return true;
