@@ -1592,6 +1592,7 @@ struct CostArgs {
     const uint32_t* positions;
     int* status;
     unsigned mask;     // length classes whose reads are counted
+    unsigned len_mask; // length classes whose reads are keyed by length alone (m / 4)
     uint32_t* cost;    // per read: min(non-popular seeds, distinct candidates, buckets - 1)
     uint32_t* read_nd; // per read: distinct candidates, or kNoCount past kCostSlots / 2
     unsigned* need;    // per class: the largest table need (distinct count, else hits)
@@ -1610,6 +1611,10 @@ __global__ void __launch_bounds__(kCostWarps * 32) k_read_cost(CostArgs a) {
         const uint64_t o0 = a.offsets[r];
         const int m = (int)(a.offsets[r + 1] - o0);
         const int q = length_class((uint64_t)m);
+        if ((a.len_mask >> q) & 1u) {
+            if (lane == 0) a.cost[r] = (uint32_t)min(m >> 2, kCostBuckets - 1);
+            continue;
+        }
         if (!((a.mask >> q) & 1u)) continue;
         const uint64_t rb = o0 - a.base0 + kReadPadBases;
         const int s = a.s;
@@ -2079,7 +2084,8 @@ struct BatchPlan {
     uint32_t* heavy_ids = nullptr;
     unsigned long long* head = nullptr;  // [0..3] class queue heads, [4] leftovers, [5..8] class counts
     uint64_t table_slots[kClasses] = {0, 0, 0, 0};  // global candidate slots each class needs
-    bool ordered[kClasses] = {false, false, false, false};  // k_read_cost + k_order_by_cost first
+    bool ordered[kClasses] = {false, false, false, false};  // k_order_by_cost before the launch
+    bool counted[kClasses] = {false, false, false, false};  // per-read table bounds (read_nd)
     const uint32_t* unsorted[kClasses] = {nullptr, nullptr, nullptr, nullptr};
     uint32_t* rcost = nullptr;
     uint32_t* rnd = nullptr;
@@ -2104,11 +2110,16 @@ static int count_candidates(const snap_index* idx, Engine* e, const uint64_t* d_
                             uint64_t n, const snap_params* p, cudaStream_t stream,
                             const BatchPrep& bp) {
     int rc;
-    e->cost_mask = 0;
+    e->cost_mask = e->len_mask = 0;
     if (param_variant(idx, p)) return SNAP_OK;
-    for (int q = 0; q < kClasses; ++q)
-        if (bp.st.cls_n[q] && block_per_read(e, bp, q)) e->cost_mask |= 1u << q;
-    if (!e->cost_mask) return SNAP_OK;
+    for (int q = 0; q < kClasses; ++q) {
+        if (!bp.st.cls_n[q]) continue;
+        if (block_per_read(e, bp, q))
+            e->cost_mask |= 1u << q;
+        else if (bp.st.cls_max_L0[q] > 31)
+            e->len_mask |= 1u << q;  // warp per read, costs spread with the square of m
+    }
+    if (!e->cost_mask && !e->len_mask) return SNAP_OK;
     if ((rc = e->rcost.ensure(n * sizeof(uint32_t), "read costs"))) return rc;
     if ((rc = e->rnd.ensure(n * sizeof(uint32_t), "candidate counts"))) return rc;
     if ((rc = e->cneed.ensure(kClasses * sizeof(unsigned), "table needs"))) return rc;
@@ -2128,6 +2139,7 @@ static int count_candidates(const snap_index* idx, Engine* e, const uint64_t* d_
     ca.positions = idx->positions;
     ca.status = &static_cast<BatchStats*>(e->stats.p)->status;
     ca.mask = e->cost_mask;
+    ca.len_mask = e->len_mask;
     ca.cost = static_cast<uint32_t*>(e->rcost.p);
     ca.read_nd = static_cast<uint32_t*>(e->rnd.p);
     ca.need = static_cast<unsigned*>(e->cneed.p);
@@ -2136,6 +2148,7 @@ static int count_candidates(const snap_index* idx, Engine* e, const uint64_t* d_
     e->launches++;
     k_read_cost<<<blocks, kCostWarps * 32, 0, stream>>>(ca);
     SNAP_CUDA(cudaGetLastError(), "cost launch");
+    if (!e->cost_mask) return SNAP_OK;  // length keys only: nothing to read back
     unsigned* h_need = reinterpret_cast<unsigned*>(static_cast<char*>(e->pin.p) + 3200);
     SNAP_CUDA(cudaMemcpyAsync(h_need, e->cneed.p, kClasses * sizeof(unsigned),
                               cudaMemcpyDeviceToHost, stream), "need copy");
@@ -2190,6 +2203,7 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
     const int seed_words = seeds_global ? 0 : 4 * a.seed_cap;
     const bool team = block_per_read(e, bp, q);
     const bool ordered = (e->cost_mask >> q) & 1u;  // counted by k_read_cost
+    const bool by_length = (e->len_mask >> q) & 1u;  // keyed by read length
     const int pwords = (Lmax <= 31 && !team) ? par_words(mmax) : 0;  // register-diagonal kernels
     const int fixed_words = 2 * a.wx + a.wt + seed_words + a.lv_ints + pwords;
     const int budget_words = 200 * 1024 / 4;  // per block; 7 words per table slot
@@ -2309,8 +2323,10 @@ static int plan_class(const snap_index* idx, Engine* e, const uint64_t* d_offset
             return rc;
         a.gseeds = static_cast<SeedRec*>(gs.p);
     }
-    // a block-per-read class runs its reads largest estimate first (k_read_cost)
-    plan->ordered[q] = ordered;
+    // a block-per-read class runs its reads largest estimate first (k_read_cost),
+    // a warp-per-read class of large limits its longest reads first
+    plan->ordered[q] = ordered || by_length;
+    plan->counted[q] = ordered;
     plan->kfn[q] = kfn;
     plan->smem[q] = smem;
     plan->blocks[q] = blocks;
@@ -2363,7 +2379,7 @@ static int plan_batch(const snap_index* idx, Engine* e, const uint64_t* d_offset
             if (!plan->use[q] || !plan->ordered[q]) continue;
             plan->unsorted[q] = plan->cl.list + plan->cl.off[q];
             plan->a[q].order = static_cast<uint32_t*>(e->order2.p) + plan->cl.off[q];
-            plan->a[q].read_nd = plan->rnd;
+            plan->a[q].read_nd = plan->counted[q] ? plan->rnd : nullptr;
         }
     }
     // global candidate tables: the class launches run side by side when two or
@@ -2618,7 +2634,7 @@ int align_batch_device(const snap_index* idx, Engine* e, const uint8_t* d_reads,
     e->last_shape = LaunchShape{0, 0, 0};  // set again by the batched form
     e->last_graph = 0;
     e->last_team = e->last_wave = e->last_wave_warps = 0;
-    e->cost_mask = 0;  // set by count_candidates for this call's batched form
+    e->cost_mask = e->len_mask = 0;  // set by count_candidates for the batched form
     e->last_light = false;
     e->last_plain = plain;
     BatchPrep bp;

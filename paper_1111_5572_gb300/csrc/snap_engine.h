@@ -42,6 +42,7 @@ struct Engine {
     DevBuf order2;     // such classes' read lists, largest estimate first
     DevBuf cneed;      // per class: the largest candidate-table need k_read_cost found
     unsigned cost_mask = 0;             // classes of this call counted by k_read_cost
+    unsigned len_mask = 0;              // warp-per-read classes ordered by read length
     unsigned cost_need[4] = {0, 0, 0, 0};  // their table needs, on the host
     // class launches that run side by side: one stream per class besides the
     // caller's, forked from and joined into the caller's stream by events
