@@ -134,9 +134,8 @@ __global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
     // votes in seed order: the candidate of every vote, and where each probe slot's end
     uint8_t evc[kLightMaxCands];
     uint8_t evend[kLightMaxSeeds];
-    unsigned long long hkey[kLightMaxCands];
-    int8_t hd[kLightMaxCands];
-    int nc = 0, nh = 0, t = 0, voted = 0, i = 0, last_np = -1;
+    // the hits are the scored candidates whose state is a distance (>= 0)
+    int nc = 0, t = 0, voted = 0, i = 0, last_np = -1;
     int d_best = kInfL, d_second = kInfL;
     unsigned long long best_key = 0;
     bool any_nonpopular = false, returned = false, draining = false;
@@ -357,18 +356,16 @@ __global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
                     c_over += (d < 0);
                     cstate[pick] = (int8_t)(d >= 0 ? d : kOver);
                     if (d >= 0) {
-                        hkey[nh] = key;
-                        hd[nh] = (int8_t)d;
-                        ++nh;
                         const unsigned long long bk = ((key >> 6) << 1) | (key & 1);
                         if (d < d_best) {
                             d_best = d;
                             best_key = key;
                             d_second = kInfL;
-                            for (int k = 0; k < nh; ++k) {
+                            for (int k = 0; k < nc; ++k) {
+                                if (cstate[k] < 0) continue;  // not a hit
                                 const unsigned long long hb =
-                                    ((hkey[k] >> 6) << 1) | (hkey[k] & 1);
-                                if (hb != bk) d_second = min(d_second, (int)hd[k]);
+                                    ((ckey[k] >> 6) << 1) | (ckey[k] & 1);
+                                if (hb != bk) d_second = min(d_second, (int)cstate[k]);
                             }
                         } else if (bk != (((best_key >> 6) << 1) | (best_key & 1))) {
                             d_second = min(d_second, d);
