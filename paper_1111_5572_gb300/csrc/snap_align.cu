@@ -109,7 +109,8 @@ k_read_stats(const uint64_t* __restrict__ offsets, uint64_t n, int s, int stride
         my.L0 = max(my.L0, dm + c - 1);
         my.nseeds = max(my.nseeds, nn);
         my.hits = hh > my.hits ? hh : my.hits;
-        my.light += (m <= (uint64_t)kLightBucketMaxM && nn <= kLightBucketMaxSeeds &&
+        my.light += (m <= (uint64_t)kLightBucketMaxM &&
+                     nn <= (stride > 1 ? kLightVariantMaxSeeds : kLightBucketMaxSeeds) &&
                      dm + c - 1 <= kLightBucketMaxL);
         const int k = length_class(m);
 #pragma unroll
@@ -364,7 +365,7 @@ struct FusedArgs {
     SeedRec* gseeds;  // per-warp seed records (seed_cap each) when not in shared memory
     uint32_t* gqbits; // per-warp q-gram bitmaps (2 x kQWords) for large limits, or NULL
     const SeedRec* hseeds;   // probe records of reads handed over by the thread-per-read
-    const uint8_t* hprobed;  // kernel (kLightBucketMaxSeeds per read), flagged per read
+    const uint8_t* hprobed;  // kernel (kLightHandoverSlots per read), flagged per read
     // per read: its distinct candidates over all seeds (k_read_cost), which bounds
     // the table it needs, or kNoCount when not counted; NULL when not computed
     const uint32_t* read_nd;
@@ -865,7 +866,7 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
         const bool reuse = a.hprobed != nullptr && a.hprobed[r] != 0;
         if (reuse) {
             for (int i = lane; i < n; i += 32) {
-                const SeedRec rec = a.hseeds[r * kLightBucketMaxSeeds + i];
+                const SeedRec rec = a.hseeds[r * kLightHandoverSlots + i];
                 wm.seeds[i] = rec;
                 if ((rec.flags & (kSeedValid | kSeedPopular)) == kSeedValid) {
                     H += (unsigned int)rec.fwd_n + rec.rc_n;
@@ -2355,7 +2356,7 @@ static int plan_batch(const snap_index* idx, Engine* e, const uint64_t* d_offset
     }
     if (plan->light) {
         if ((rc = light_prepare())) return rc;
-        if ((rc = e->hseeds.ensure(n * kLightBucketMaxSeeds * sizeof(SeedRec), "handed-over probes")))
+        if ((rc = e->hseeds.ensure(n * kLightHandoverSlots * sizeof(SeedRec), "handed-over probes")))
             return rc;
         if ((rc = e->hprobed.ensure(n, "handed-over flags"))) return rc;
     }

@@ -97,7 +97,12 @@ inline int grid_cap(int sms, uint64_t n, int threads) {
 
 // thread-per-read kernel (snap_light.cu): limits of the reads it takes
 constexpr int kLightBucketMaxM = 128;
-constexpr int kLightBucketMaxSeeds = 6;
+constexpr int kLightBucketMaxSeeds = 6;    // probe slots on a plain index
+// probe slots on a strided index (stride 2: nine probes for a 100 bp read) or with
+// the seeds-first variant; its kernel keeps these records in local memory
+constexpr int kLightVariantMaxSeeds = 10;
+// probe records per read in the hand-over buffer (room for either kernel)
+constexpr int kLightHandoverSlots = 10;
 constexpr int kLightBucketMaxL = 15;
 int light_prepare();
 int launch_light(const snap_index* idx, Engine* e, const uint64_t* d_offsets, uint64_t n,

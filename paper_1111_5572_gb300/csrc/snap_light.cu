@@ -26,7 +26,6 @@
 namespace snapgpu {
 
 constexpr int kLightMaxM = kLightBucketMaxM;
-constexpr int kLightMaxSeeds = kLightBucketMaxSeeds;
 constexpr int kLightMaxL = kLightBucketMaxL;
 // Index hits a read may have and stay here.  The per-thread candidate arrays live
 // in local memory, whose footprint competes with shared memory for L1: 8 measured
@@ -73,7 +72,7 @@ struct LightArgs {
     snap_result* out;
     uint32_t* heavy_ids;
     unsigned long long* heavy_count;
-    SeedRec* hseeds;   // probe records of handed-over reads (kLightMaxSeeds per read)
+    SeedRec* hseeds;   // probe records of handed-over reads (kLightHandoverSlots per read)
     uint8_t* hprobed;  // per read: 1 when hseeds holds them
     int* status;
     DevCounters* ctr;
@@ -123,6 +122,7 @@ __global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
     int m = 0, n = 0, dmax = 0;
     bool heavy = false;  // the warp-per-read kernel takes the read
     bool live = false;   // Algorithm 1 still running here
+    constexpr int kLightMaxSeeds = VARIANT ? kLightVariantMaxSeeds : kLightBucketMaxSeeds;
     SeedRec seeds[kLightMaxSeeds];
     // candidates: key 2p + strand, the distance at L0 found up front (exact d,
     // kOver, or kLaneGaveUp when it needs a fifth round), votes, and the state
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256, 5) k_align_light(LightArgs a) {
             heavy = H > (unsigned)kLightMaxCands;
             if (heavy && a.hseeds) {  // handed over after probing: the warp kernel
                 for (int q = 0; q < n; ++q)  // starts from these records
-                    a.hseeds[r * kLightMaxSeeds + q] = seeds[q];
+                    a.hseeds[r * kLightHandoverSlots + q] = seeds[q];
                 a.hprobed[r] = 1;
             }
             if (!heavy) {
