@@ -452,8 +452,9 @@ __host__ __device__ constexpr int par_union_words(int mmax) {
     return 2 * kParMaxCands > 32 * par_window_words(mmax) ? 2 * kParMaxCands
                                                            : 32 * par_window_words(mmax);
 }
+// the lanes' diagonals are 16-bit (reads of the parallel drain are below 2^14 bases)
 __host__ __device__ constexpr int par_words(int mmax) {
-    return par_union_words(mmax) + kParMaxCands + 32 * (2 * kParMaxL + 3);
+    return par_union_words(mmax) + kParMaxCands + (32 * (2 * kParMaxL + 3) + 1) / 2;
 }
 
 // ---------------------------------------------------------------------------
@@ -1012,7 +1013,7 @@ __device__ __forceinline__ void align_one_read(const FusedArgs& a, const WarpMem
                 unsigned long long* upk = reinterpret_cast<unsigned long long*>(wm.par);
                 uint32_t* Tp = wm.par;  // after ranking: the lanes' windows
                 uint32_t* order = wm.par + par_union_words(a.par_mmax);
-                int* Rp = reinterpret_cast<int*>(order + kParMaxCands);
+                int16_t* Rp = reinterpret_cast<int16_t*>(order + kParMaxCands);
                 // unscored candidates, packed as in table_pick (distinct keys)
                 int U = 0;
                 for (int j0 = 0; j0 < nd; j0 += 32) {

@@ -250,20 +250,22 @@ __device__ __forceinline__ uint32_t get16s(const uint32_t* w, int i, int stride)
 // in increasing order, updated in place in R (round e-1's value is only read for
 // |k| <= e-1, so R needs no initialisation).  X and T are packed at word strides
 // xs and ts.  Returns kLaneGaveUp instead of starting round max_rounds (a caller
-// that hands costly reads elsewhere); R holds 2 min(L, max_rounds - 1) + 3 ints
-// at stride rs.
+// that hands costly reads elsewhere); R holds 2 min(L, max_rounds - 1) + 3 values
+// at stride rs, 32-bit, or 16-bit (RT = int16_t) for reads shorter than 2^14 bases
+// and L < 2^13 (an invalid diagonal then stays negative through its increments).
 constexpr int kLaneGaveUp = -3;
+template <typename RT = int>
 __device__ __forceinline__ int lv_lane(const uint32_t* X, int xs, int m, const uint32_t* Tw, int ts,
-                                       int tb, int n, int L, int* R, int rs,
+                                       int tb, int n, int L, RT* R, int rs,
                                        int max_rounds = 0x7fffffff) {
-    constexpr int NEG = -0x40000000;
+    constexpr int NEG = sizeof(RT) == 2 ? -0x4000 : -0x40000000;
     if (L < 0) return kOver;
     const int off = min(L, max_rounds - 1) + 1;  // R index of diagonal k is k + off
     for (int e = 0; e <= L; ++e) {
         if (e >= max_rounds) return kLaneGaveUp;
         int left_old = NEG;
         for (int k = -e; k <= e; ++k) {
-            int* slot = R + (k + off) * rs;
+            RT* slot = R + (k + off) * rs;
             const int cur_old = (k >= -(e - 1) && k <= e - 1) ? *slot : NEG;
             int r;
             if (e == 0) {
@@ -276,7 +278,7 @@ __device__ __forceinline__ int lv_lane(const uint32_t* X, int xs, int m, const u
             if (r > m) r = m;
             if (r + k > n) r = n - k;
             if (r < 0 || r + k < 0) {
-                *slot = NEG;
+                *slot = (RT)NEG;
                 continue;
             }
             for (;;) {
@@ -291,7 +293,7 @@ __device__ __forceinline__ int lv_lane(const uint32_t* X, int xs, int m, const u
                 r += adv;
                 if (adv < 16) break;
             }
-            *slot = r;
+            *slot = (RT)r;
             if (r >= m) return e;
         }
     }
